@@ -1,0 +1,329 @@
+"""Pins of the FP64 oracle against what the thesis and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a closed form, an
+invariant, a textbook routine, a published constant, or a convergence order,
+chosen so that a dropped term, a wrong sign/index or a transposed operand in
+the oracle fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_07104_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+def P(**kw):
+    p = dict(W.DEFAULT_PARAMS)
+    p.update(kw)
+    return p
+
+
+# --------------------------------------------------------------------------
+# Subcellular model
+# --------------------------------------------------------------------------
+
+def test_rest_gates_match_published_hh1952_values():
+    g = golden("hh1952_rest.txt")
+    m, h, n = oracle.gates_inf(P(), -75.0)
+    assert abs(m - g["m_rest"]) < 1e-5
+    assert abs(h - g["h_rest"]) < 1e-5
+    assert abs(n - g["n_rest"]) < 1e-5
+
+
+def test_exact_leak_reversal_close_to_published_value():
+    # Deriving E_L so that rest is exact must land within a few hundredths of
+    # a mV of HH's published leak reversal (which made rest nearly stationary).
+    g = golden("hh1952_rest.txt")
+    p = P()
+    el = oracle.leak_reversal_exact(p)
+    assert abs((el - p["Vrest"]) - g["leak_reversal_above_rest_mV"]) < 0.03
+
+
+def test_rest_is_a_fixed_point_of_the_rhs():
+    p = P()
+    y = np.array([p["Vrest"], *oracle.gates_inf(p, p["Vrest"])])
+    assert np.max(np.abs(oracle.hh_rhs(p, y))) <= 1e-13
+    # with the published (not exact) leak reversal, rest drifts: the exact
+    # derivation is what makes the fixed point
+    y2 = oracle.hh_rhs(P(EL=p["Vrest"] + 10.613), y)
+    assert abs(y2[0]) > 1e-3
+
+
+def test_rest_fiber_stays_at_rest_through_split_steps():
+    p = P()
+    n = 50
+    st = oracle.init_state(p, n, None)
+    ref = st.copy()
+    oracle.run(p, [n], [0], [25], [0, 0], [], st, 0, 10, n_threads=1)
+    assert np.max(np.abs(st - ref)) <= 1e-12
+
+
+def test_gate_rhs_sign_and_rates_singularities():
+    p = P()
+    # removable singularities: alpha_m at u = 25 (V = -50) has limit 1/ms,
+    # alpha_n at u = 10 (V = -65) has limit 0.1/ms
+    for eps in (0.0, 1e-9, -1e-9, 1e-6):
+        r = oracle.hh_rates(p, -50.0 + eps)
+        assert abs(r[0] - (1.0 + eps / 20.0)) < 1e-9
+        r = oracle.hh_rates(p, -65.0 + eps)
+        assert abs(r[4] - (0.1 + eps / 200.0)) < 1e-9
+    # the gate equation relaxes g towards alpha/(alpha+beta) at fixed V:
+    # dg/dt must vanish at g_inf and be positive below it
+    V = -40.0
+    ginf = oracle.gates_inf(p, V)
+    y = np.array([V, *ginf])
+    f = oracle.hh_rhs(p, y)
+    assert np.max(np.abs(f[1:])) < 1e-14
+    f2 = oracle.hh_rhs(p, np.array([V, *(0.5 * ginf)]))
+    assert np.all(f2[1:] > 0)
+
+
+def test_ap_shape_matches_thesis_facts():
+    facts = golden("thesis_ap_facts.txt")
+    w = W.single_fiber(t_end_ms=35.0, n_nodes=201)
+    _, s = oracle.run_workload(w, sample_every=1)
+    c = int(w.junction[0])
+    v = s[:, c]
+    assert facts["peak_mV_lo"] <= v.max() <= facts["peak_mV_hi"]
+    k30 = int(round(facts["equilibrium_after_ms"] / w.params["dt_split"]))
+    assert np.max(np.abs(s[k30:, :] - facts["resting_mV"])) <= facts["equilibrium_band_mV"]
+    # two action potentials travel out from the junction (cf. fig:hodgkin_huxley_over_mesh)
+    mid = s[int(round(2.5 / w.params["dt_split"]))]
+    assert mid[:c].max() > 0 and mid[c + 1:].max() > 0 and mid[c] < 0
+
+
+# --------------------------------------------------------------------------
+# Tridiagonal solve and the CN system
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 13, 21, 34, 50])
+def test_thomas_matches_dense_lu(n):
+    rng = np.random.default_rng(n)
+    a = rng.uniform(-1, 1, n)
+    c = rng.uniform(-1, 1, n)
+    b = np.abs(a) + np.abs(c) + rng.uniform(0.1, 2.0, n)  # diagonally dominant
+    b *= rng.choice([-1.0, 1.0], n)
+    d = rng.normal(size=n)
+    A = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    x_ref = np.linalg.solve(A, d)
+    x = oracle.thomas(a, b, c, d)
+    assert np.max(np.abs(x - x_ref)) <= 1e-12 * max(1.0, np.max(np.abs(x_ref)))
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 50])
+@pytest.mark.parametrize("h", [0.01, 0.0025])
+def test_cn_system_matches_fem_assembly(n, h):
+    """Assemble linear-element stiffness and mass, lump the mass by row sums
+    (sec:mass_lumping), and form eq:lumping_crank_nicolson_2 densely; the
+    oracle's bands and RHS must be exactly that system (incl. Neumann ends)."""
+    p = P(h=h)
+    c = p["sigma_eff"] / (p["Am"] * p["Cm"])
+    dt = 1.5e-3
+    K = np.zeros((n, n))
+    M = np.zeros((n, n))
+    Ke = -(1.0 / h) * np.array([[1.0, -1.0], [-1.0, 1.0]])  # K_kj = -int phi_j' phi_k'
+    Me = (h / 6.0) * np.array([[2.0, 1.0], [1.0, 2.0]])
+    for e in range(n - 1):
+        idx = np.array([e, e + 1])
+        K[np.ix_(idx, idx)] += Ke
+        M[np.ix_(idx, idx)] += Me
+    ML = np.diag(M.sum(axis=1))
+    L = c * np.linalg.solve(ML, K)
+    Alhs = np.eye(n) - 0.5 * dt * L
+    Brhs = np.eye(n) + 0.5 * dt * L
+    V = np.random.default_rng(1).normal(size=n) * 10 - 70
+    a, b, cc, d = oracle.cn_system(p, V, dt)
+    Adense = np.diag(b) + np.diag(a[1:], -1) + np.diag(cc[:-1], 1)
+    assert np.max(np.abs(Adense - Alhs)) < 1e-13
+    assert np.max(np.abs(d - Brhs @ V)) < 1e-11
+
+
+@pytest.mark.parametrize("k", [1, 2, 7])
+def test_cn_cosine_mode_closed_form(k):
+    """v_k(i) = cos(k pi i / (N-1)) is an eigenvector of the lumped Neumann
+    operator with lambda_k = -(4c/h^2) sin^2(k pi / (2(N-1))); m CN steps
+    scale it by ((1 + lambda dt/2)/(1 - lambda dt/2))^m."""
+    p = P()
+    n, dt, m = 64, 1.5e-3, 40
+    c = p["sigma_eff"] / (p["Am"] * p["Cm"])
+    i = np.arange(n)
+    v = np.cos(k * np.pi * i / (n - 1))
+    lam = -(4 * c / p["h"] ** 2) * np.sin(k * np.pi / (2 * (n - 1))) ** 2
+    g = ((1 + lam * dt / 2) / (1 - lam * dt / 2)) ** m
+    x = v.copy()
+    for _ in range(m):
+        x = oracle.cn_step(p, x, dt)
+    assert np.max(np.abs(x - g * v)) <= 1e-12
+
+
+def test_cn_conserves_lumped_mass_weighted_sum():
+    p = P()
+    rng = np.random.default_rng(7)
+    for n in (2, 3, 17, 300):
+        V = rng.normal(size=n) * 20 - 60
+        w = np.ones(n)
+        if n > 1:
+            w[0] = w[-1] = 0.5
+        s0 = w @ V
+        x = V.copy()
+        for _ in range(25):
+            x = oracle.cn_step(p, x, 1.5e-3)
+        assert abs(w @ x - s0) <= 1e-12 * abs(s0)
+        if n > 3:  # the plain sum is *not* invariant
+            assert abs(x.sum() - V.sum()) > 1e-9
+
+
+# --------------------------------------------------------------------------
+# Stimulus: charge balance with the ionic currents switched off
+# --------------------------------------------------------------------------
+
+def _charge_run(n, junction, fire, n_steps, **kw):
+    p = P(gNa=0.0, gK=0.0, gL=0.0, EL=0.0, **kw)
+    st = oracle.init_state(p, n, None)
+    V0 = st[:n].copy()
+    oracle.run(p, [n], [0], [junction], [0, len(fire)], np.asarray(fire, float), st, 0, n_steps, n_threads=1)
+    w = np.ones(n)
+    if n > 1:
+        w[0] = w[-1] = 0.5
+    return p, w @ (st[:n] - V0)
+
+
+def test_stimulus_charge_balance_centre():
+    # Heun is exact for a constant RHS and CN conserves the weighted sum, so
+    # the weighted sum grows by A/Cm per on-substep at each of the 3 nodes.
+    p, q = _charge_run(101, 50, [0.0], 40)
+    P_sub = round(p["stim_duration"] / p["dt_0d"])
+    assert P_sub == 100
+    expect = 3 * P_sub * p["dt_0d"] * p["stim_amplitude"] / p["Cm"]
+    assert abs(q - expect) <= 1e-9 * expect
+
+
+def test_stimulus_window_boundaries_and_or_semantics():
+    dt0 = W.DEFAULT_PARAMS["dt_0d"]
+    A = W.DEFAULT_PARAMS["stim_amplitude"]
+    per_sub = 3 * dt0 * A
+    # stopping after 33 split steps = 99 substeps: the pulse is still on
+    _, q = _charge_run(101, 50, [0.0], 33)
+    assert abs(q - 99 * per_sub) < 1e-9 * q
+    # a firing at t = 0.05 ms starts at substep 50; two overlapping pulses
+    # cover substeps [0, 150): OR-ed, not summed
+    _, q = _charge_run(101, 50, [0.0, 0.05], 60)
+    assert abs(q - 150 * per_sub) < 1e-9 * q
+    # disjoint pulses add up
+    _, q = _charge_run(101, 50, [0.0, 0.3], 200)
+    assert abs(q - 200 * per_sub) < 1e-9 * q
+    # a firing after the simulated interval injects nothing
+    _, q = _charge_run(101, 50, [10.0], 30)
+    assert abs(q) < 1e-8  # only CN rounding on a weighted sum of about -7500
+
+
+def test_stimulus_at_fiber_end_is_clipped():
+    dt0 = W.DEFAULT_PARAMS["dt_0d"]
+    A = W.DEFAULT_PARAMS["stim_amplitude"]
+    # junction at node 0: nodes 0 (weight 1/2) and 1 (weight 1) only
+    _, q = _charge_run(40, 0, [0.0], 40)
+    assert abs(q - 1.5 * 100 * dt0 * A) < 1e-9 * q
+    # single-node fiber: no diffusion, V grows linearly by A/Cm per ms
+    _, q = _charge_run(1, 0, [0.0], 40)
+    assert abs(q - 100 * dt0 * A) < 1e-9 * q
+
+
+# --------------------------------------------------------------------------
+# Convergence orders (eq:heun and eq:monodomain_strang are second order)
+# --------------------------------------------------------------------------
+
+def _observed_orders(errs):
+    errs = np.asarray(errs)
+    return np.log2(errs[:-1] / errs[1:])
+
+
+def test_heun_is_second_order_on_a_single_cell():
+    # N = 1: pure 0D; a 15 mV depolarisation starts a space-clamped AP
+    t_end = 1.0
+    finals = {}
+    for dt in (0.02, 0.01, 0.005, 0.02 / 64):
+        p = P(dt_split=dt, dt_0d=dt, dt_1d=dt / 2)
+        st = oracle.init_state(p, 1, np.array([p["Vrest"] + 15.0], np.float32))
+        oracle.run(p, [1], [0], [0], [0, 0], [], st, 0, int(round(t_end / dt)), n_threads=1)
+        finals[dt] = st.copy()
+    ref = finals[0.02 / 64]
+    errs = [np.max(np.abs(finals[dt] - ref)) for dt in (0.02, 0.01, 0.005)]
+    orders = _observed_orders(errs)
+    assert np.all((orders > 1.8) & (orders < 2.2)), (errs, orders)
+
+
+def test_strang_heun_cn_is_second_order_on_a_fiber():
+    # smooth Gaussian bump of 30 mV, no pulsed stimulus, 0.96 ms horizon (a
+    # whole number of steps for every dt); dt_0d = dt/3 and dt_1d = dt/2 as in
+    # the configurations
+    n = 101
+    x = np.arange(n) * 0.01
+    t_end = 0.96
+    finals = {}
+    dts = (0.012, 0.006, 0.003)
+    ref_dt = 0.012 / 32
+    for dt in dts + (ref_dt,):
+        p = P(dt_split=dt, dt_0d=dt / 3, dt_1d=dt / 2)
+        vm0 = (p["Vrest"] + 30.0 * np.exp(-((x - 0.5) / 0.1) ** 2)).astype(np.float32)
+        st = oracle.init_state(p, n, vm0)
+        oracle.run(p, [n], [0], [50], [0, 0], [], st, 0, int(round(t_end / dt)), n_threads=1)
+        finals[dt] = st.copy()
+    ref = finals[ref_dt]
+    errs = [np.max(np.abs(finals[dt][:n] - ref[:n])) for dt in dts]
+    orders = _observed_orders(errs)
+    assert np.all((orders > 1.8) & (orders < 2.2)), (errs, orders)
+
+
+# --------------------------------------------------------------------------
+# Propagation velocity (sec:action_potential_velocity)
+# --------------------------------------------------------------------------
+
+def _velocity(h, sigma_scale=1.0, length_cm=4.0, t_end=12.0):
+    n = int(round(length_cm / h)) + 1
+    p = P(h=h, sigma_eff=W.DEFAULT_PARAMS["sigma_eff"] * sigma_scale,
+          stim_amplitude=W.DEFAULT_PARAMS["stim_amplitude"] * 0.01 / h)  # same charge per length
+    dt = p["dt_split"]
+    c = (n - 1) // 2
+    st = oracle.init_state(p, n, None)
+    s = oracle.run(p, [n], [0], [c], [0, 1], np.array([0.0]), st, 0, int(round(t_end / dt)), sample_every=1)
+    # arrival time of the first upward 0 mV crossing, linearly interpolated
+    def arrival(i):
+        col = s[:, i]
+        k = np.nonzero((col[:-1] < 0) & (col[1:] >= 0))[0][0]
+        return (k + 1 + (0 - col[k]) / (col[k + 1] - col[k])) * dt
+    half = (n - 1) // 2
+    i1, i2 = c + half // 4, c + (3 * half) // 4
+    return (i2 - i1) * h / (arrival(i2) - arrival(i1))
+
+
+@pytest.mark.slow
+def test_velocity_is_stable_under_mesh_refinement():
+    v = {h: _velocity(h) for h in (0.02, 0.01, 0.005)}
+    # converging: the 0.01 -> 0.005 change is small and smaller than 0.02 -> 0.01
+    d1 = abs(v[0.01] - v[0.02]) / v[0.01]
+    d2 = abs(v[0.005] - v[0.01]) / v[0.005]
+    assert d2 <= 0.02, v
+    assert d2 < d1, v
+
+
+@pytest.mark.slow
+def test_velocity_scales_with_square_root_of_diffusivity():
+    # x -> 2x, c -> 4c leaves the monodomain equation invariant: v ~ sqrt(c)
+    v1 = _velocity(0.005)
+    v4 = _velocity(0.005, sigma_scale=4.0, length_cm=8.0)
+    assert abs(v4 / v1 - 2.0) <= 0.03, (v1, v4)
