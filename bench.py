@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: fiber node-updates/s of the full Strang split step on GB300.
+
+Workload (per GPU): the 7744-fiber bundle (88 x 88 fibers x 1481 nodes,
+h = 0.01 cm, 100 motor units with exponential sizes, Poisson firing at
+10-30 Hz), seeded synthetic inputs.  One benchmark "step" is one split step
+(CN half, 3 Heun substeps, CN half) of every fiber.  The timed region runs
+--steps split steps through the library's CUDA-graph step loop with the state
+already resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank simulates its own bundle (seed 2 + rank) on
+its own GPU with no data-path communication (fibers are independent): weak
+scaling, whole-job value = sum of node-updates over ranks / max time.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference
+implementation of this method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2107_07104_gb300 import workloads as W  # noqa: E402
+
+METRIC = "fiber node-updates/s (full split step) at max|ΔVm|≤0.5 mV, plain FP32 vs surrogate"
+UNIT = "node-updates/s"
+WORKLOAD = "bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz"
+# Algorithmic work per node-update of the plain FP32 path:
+BYTES_PER_NODE_UPDATE = 32.0     # read + write V, m, h, n (FP32) once per split step
+FMA_OPS_PER_NODE_UPDATE = 238.0  # FP32 FMA-pipe operations of the method per split step
+MUFU_OPS_PER_NODE_UPDATE = 42.0  # 2^x and 1/x special-function operations per split step
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl"
+        try:
+            import torch
+            torch.cuda.set_device(local)
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(w, fibers: int, steps: int):
+    """Node-updates/s of the FP64 oracle on the first `fibers` fibers, all host cores."""
+    import oracle
+    sub = w.subset(np.arange(min(fibers, w.n_fibers)))
+    state = oracle.init_state(sub.params, sub.total_nodes, sub.vm0)
+    cores = cpu_cores()
+    t0 = time.perf_counter()
+    oracle.run(sub.params, sub.n_nodes, sub.mu_of_fiber, sub.junction, sub.mu_offsets, sub.fire_times, state, 0,
+               steps, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return sub.total_nodes * steps / dt, dt, cores, sub.total_nodes
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
+    import oracle
+    cores = cpu_cores()
+    # size the per-step sample so that warm-up + timed steps take about 100 s
+    rate, _, _, _ = oracle_rate(w, 64, 2)
+    fibers = int(np.clip(rate * 100.0 / (1481.0 * (args.steps + args.warmup)), 16, 1024))
+    sub = w.subset(np.arange(fibers))
+    state = oracle.init_state(sub.params, sub.total_nodes, sub.vm0)
+    step = 0
+    for _ in range(args.warmup):
+        oracle.run(sub.params, sub.n_nodes, sub.mu_of_fiber, sub.junction, sub.mu_offsets, sub.fire_times, state,
+                   step, 1, n_threads=cores)
+        step += 1
+    t0 = time.perf_counter()
+    oracle.run(sub.params, sub.n_nodes, sub.mu_of_fiber, sub.junction, sub.mu_offsets, sub.fire_times, state, step,
+               args.steps, n_threads=cores)
+    dt = time.perf_counter() - t0
+    value = sub.total_nodes * args.steps / dt
+    sample = f"first {fibers} of 7744 fibers x 1481 nodes, {args.steps} split steps, FP64 oracle"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, world, rank, local, dist):
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.bundle_7744(seed=2 + rank, t_end_ms=20.0)
+    total = w.total_nodes
+    stream = torch.cuda.Stream(device=dev)
+    tuning = dict(nodes_per_thread=args.nodes_per_thread, warps_per_cta=args.warps_per_cta,
+                  steps_per_launch=args.steps_per_launch, graph_steps=args.graph_steps)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident timing: K split steps, state already in HBM --------
+    fib = F.Fibers.from_workload(w, tuning=tuning, stream=stream)
+    if args.autotune:
+        fib.autotune(20)
+    fib.step(args.warmup)
+    fib.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = fib.kernel_launches
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        fib.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = fib.kernel_launches - launches0
+    tune = fib.tuning
+    vm = fib.read_vm()
+    finite = bool(np.isfinite(vm).all())
+    fib.close()
+    S = tune["steps_per_launch"]
+    G = tune["graph_steps"]
+    split_launches = 0
+    rem = args.steps
+    if G > 0:
+        split_launches += (rem // G) * ((G + S - 1) // S)
+        rem %= G
+    split_launches += (rem + S - 1) // S
+
+    t = torch.tensor([ms / 1e3], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    node_updates = float(total) * args.steps * world
+    value = node_updates / t_max
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    host_out = np.empty(total, np.float32)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    fib2 = F.Fibers.from_workload(w, tuning=tune, stream=stream)
+    fib2.step(args.steps)
+    fib2.read_vm(host_out)
+    t_e2e = time.perf_counter() - t0
+    fib2.close()
+    te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = node_updates / float(te.item())
+    h2d = 12 * w.n_fibers + 8 * (w.mu_offsets.size + w.fire_times.size)
+    d2h = 4 * total
+
+    if rank != 0:
+        return 0
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_gpu_rate = float(total) * args.steps / (ms / 1e3)
+    # ALU roofline: node-updates/s if the binding FP32 or MUFU pipe ran at its
+    # full rate on every SM at the maximum SM clock.
+    alu_peak = n_sm * sm_max * min(FP32_LANES_PER_SM / FMA_OPS_PER_NODE_UPDATE,
+                                   MUFU_LANES_PER_SM / MUFU_OPS_PER_NODE_UPDATE)
+    kernel_ms = ms / max(split_launches, 1)
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "split_step_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                pj = json.load(f)
+            if pj.get("steps_per_launch") == S and pj.get("nodes_per_thread") == tune["nodes_per_thread"]:
+                traffic = pj.get("dram_bytes_per_launch_full_bundle")
+        except (OSError, ValueError):
+            traffic = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, dt, cores, nodes = oracle_rate(w, args.cpu_fibers, args.cpu_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_fibers} of 7744 fibers x 1481 nodes, {args.cpu_steps} split steps "
+                         f"({dt:.1f} s of FP64 oracle on {cores} threads)"}
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fibers": int(w.n_fibers), "nodes": int(total),
+                   "path": "plain FP32 (HH Heun x3 + CN/partitioned Thomas x2)",
+                   "tuning": tune, "parallelism": f"replicas x{world} (independent fibers)",
+                   "l2": f"state {4 * 4 * total / 1e6:.0f} MB > 129 MB L2, streamed from HBM by every launch"},
+        "roofline": {
+            "bound": "alu", "achieved": per_gpu_rate / 1e9, "peak": alu_peak / 1e9, "unit": "Gnode-updates/s",
+            "frac": per_gpu_rate / alu_peak, "traffic": traffic,
+            "kernel": "split_step_kernel", "kernel_ms_per_launch": kernel_ms,
+            "algorithmic_bytes_per_launch": BYTES_PER_NODE_UPDATE * total * S,
+            "peak_derivation": f"{n_sm} SMs x {sm_max / 1e6:.0f} MHz x min(128 FP32 lanes / "
+                               f"{FMA_OPS_PER_NODE_UPDATE:.0f} FMA ops, 16 MUFU lanes / "
+                               f"{MUFU_OPS_PER_NODE_UPDATE:.0f} MUFU ops) per node-update",
+            "hbm_equivalent": {"achieved_gbs": per_gpu_rate * BYTES_PER_NODE_UPDATE / 1e9, "peak_gbs": hbm_peak,
+                               "frac": per_gpu_rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak,
+                               "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps,
+                "includes": "fibers_create + set_stimulus_times from host arrays, step(K), read_vm to host"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "finite": finite,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nodes-per-thread", type=int, default=0)
+    ap.add_argument("--warps-per-cta", type=int, default=0)
+    ap.add_argument("--steps-per-launch", type=int, default=0)
+    ap.add_argument("--graph-steps", type=int, default=1000)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--cpu-fibers", type=int, default=256)
+    ap.add_argument("--cpu-steps", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local, dist = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_gpu(args, world, rank, local, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

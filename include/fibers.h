@@ -1,0 +1,179 @@
+/*
+ * fibers.h -- C ABI of the GB300 (sm_103a) fiber monodomain library.
+ *
+ * The library advances many independent 1D muscle fibers through the
+ * operator-split monodomain model of Maier 2021 ("Scalable Biophysical
+ * Simulations of the Neuromuscular System"):
+ *
+ *   dV/dt = (sigma_eff d2V/dx2 - Am I_ion(V, y)) / (Am Cm)   (eq:monodomain)
+ *
+ * with homogeneous Neumann ends (eq:monodomain_bc1), the Hodgkin-Huxley
+ * subcellular model (sec:subcelullar_model, eq:subcellular), lumped-mass
+ * linear finite elements (sec:mass_lumping), Crank-Nicolson diffusion
+ * (eq:lumping_crank_nicolson_2) solved per fiber as a tridiagonal system
+ * (sec:improved_parallel_solver_for_fiber_based), Heun reaction steps
+ * (eq:heun) and Strang splitting (eq:monodomain_strang): per split step
+ * dt_split one diffusion half (dt_split/2), the reaction over dt_split in
+ * Heun substeps of dt_0d, and a second diffusion half.  Fibers are driven by
+ * motor-unit (MU) firing trains at their neuromuscular junction
+ * (sec:stimulation_times_callbacks).
+ *
+ * Units: cm, ms, mV, uA/cm^2, uF/cm^2, mS/cm^2, mS/cm.
+ *
+ * Conventions for every call:
+ *   - Every function returns a fib_status; nothing throws across the ABI.
+ *     A failing call leaves a message readable with fibers_last_error().
+ *   - The library copies every input array; the caller keeps ownership of
+ *     its buffers.  A context owns all device memory it allocates and frees
+ *     it in fibers_destroy().
+ *   - Work is enqueued on the stream given to fibers_create (NULL: the
+ *     legacy default stream).  step() is asynchronous; errors raised by the
+ *     device (non-finite state) are reported by the next synchronising call
+ *     (read_vm, fibers_read_state, fibers_synchronize, fibers_stats).
+ *   - Node arrays are in "ragged order": the nodes of fiber 0, then fiber 1,
+ *     and so on, sum(n_nodes) entries in total.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef FIBERS_H_
+#define FIBERS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fib_ctx fib_ctx;
+
+typedef enum {
+  FIB_OK = 0,
+  FIB_EINVAL = 1,      /* bad argument (message says which) */
+  FIB_ENOMEM = 2,      /* device or host allocation failed */
+  FIB_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+  FIB_ENONFINITE = 4,  /* the state became NaN/Inf; it stays readable */
+  FIB_ETIMEOUT = 5,    /* a bounded host wait gave up */
+  FIB_ESTATE = 6,      /* call not valid in the current state */
+  FIB_ENOTSUP = 7      /* valid request that this build does not support */
+} fib_status;
+
+/* Solve modes. */
+enum {
+  FIB_MODE_FP32 = 0,         /* FP32 state and arithmetic */
+  FIB_MODE_FP64_THOMAS = 1,  /* FP32 state and reaction; tridiagonal solve in FP64 */
+  FIB_MODE_SURROGATE = 2     /* reaction step by a learned MLP with HH fallback */
+};
+
+/* Model and discretisation parameters (sec:subcelullar_model, eq:monodomain,
+ * eq:monodomain_strang).  ENa, EK and EL are absolute reversal potentials;
+ * EL = NaN asks the library to derive it so that (Vrest, m_inf, h_inf, n_inf)
+ * is an exact rest state.  The HH rates are those of Hodgkin & Huxley 1952 in
+ * the depolarisation u = V - Vrest.  dt_split / dt_0d and (dt_split/2) /
+ * dt_1d must be whole numbers.  A firing at time t_f switches the stimulus
+ * on for Heun substeps k with k_f <= k < k_f + P, k_f = round(t_f / dt_0d)
+ * (half to even), P = round(stim_duration / dt_0d), at junction nodes
+ * j - stim_half_width .. j + stim_half_width (clipped to the fiber).  */
+typedef struct {
+  double Cm, gNa, gK, gL, ENa, EK, EL, Vrest;
+  double sigma_eff, Am, h;
+  double dt_split, dt_0d, dt_1d;
+  double stim_amplitude, stim_duration;
+  int32_t stim_half_width;
+  int32_t mode;     /* FIB_MODE_* */
+  int32_t flags;    /* reserved, must be 0 */
+  int32_t reserved; /* must be 0 */
+} fib_params;
+
+/* Launch shape.  Zero fields mean "choose automatically". */
+typedef struct {
+  int32_t nodes_per_thread;  /* K: 4, 8, 12 or 16 nodes held in registers per thread */
+  int32_t warps_per_cta;     /* CTA size in warps (1..32); fibers are packed by whole warps */
+  int32_t steps_per_launch;  /* split steps each kernel launch keeps on chip */
+  int32_t graph_steps;       /* split steps per captured CUDA graph (0 = no graphs) */
+} fib_tuning;
+
+/* Creates a context for n_fibers fibers and copies the inputs to the device.
+ *   p             model parameters (copied).
+ *   n_fibers      >= 0.
+ *   n_nodes       [n_fibers] nodes per fiber, >= 1 (mesh width p->h).
+ *   mu_of_fiber   [n_fibers] motor unit of each fiber, or -1 (never stimulated).
+ *   junction_node [n_fibers] neuromuscular-junction node, 0 <= j < n_nodes.
+ *   vm0           [sum(n_nodes)] initial V in mV, or NULL for V = Vrest.
+ *                 Gates start at their steady state at Vrest.
+ *   tuning        launch shape, or NULL for automatic.
+ *   cuda_stream   cudaStream_t to run on, or NULL.
+ *   out           receives the context (NULL on failure).
+ * Errors: FIB_EINVAL (bad parameter, fiber too long for the tuning),
+ * FIB_ENOMEM, FIB_ECUDA.  Thesis: the inputs FastMonodomainSolver sends to
+ * the GPU once (section "Code Generation for GPUs": initial state, junctions, fiber
+ * to MU map) and eq:discretized_fibers (independent per-fiber systems). */
+fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n_nodes,
+                         const int32_t* mu_of_fiber, const int32_t* junction_node, const float* vm0,
+                         const fib_tuning* tuning, void* cuda_stream, fib_ctx** out);
+
+/* Sets the MU firing trains (sec:stimulation_times_callbacks).
+ *   n_mu          number of motor units; MU ids in mu_of_fiber must be < n_mu.
+ *   offsets       [n_mu + 1] CSR offsets into fire_times_ms (offsets[0] = 0).
+ *   fire_times_ms firing times in ms, ascending within each MU, >= 0.
+ * Replaces any previous trains.  Before the first call no fiber is
+ * stimulated.  Errors: FIB_EINVAL (unsorted, negative, bad offsets). */
+fib_status set_stimulus_times(fib_ctx* ctx, int32_t n_mu, const int64_t* offsets,
+                              const double* fire_times_ms);
+
+/* Enqueues n_steps >= 0 Strang split steps (eq:monodomain_strang) for all
+ * fibers.  Split step i covers t in [i dt_split, (i+1) dt_split); i counts
+ * from 0 at creation (or the index given to fibers_write_state).  Returns
+ * after enqueueing.  Errors: FIB_EINVAL (n_steps < 0), FIB_ECUDA. */
+fib_status step(fib_ctx* ctx, int64_t n_steps);
+
+/* Copies V (mV, float) of every node in ragged order into out.
+ *   capacity       elements available in out (>= sum(n_nodes)).
+ *   out_is_device  0: out is host memory; 1: device memory of the context's GPU.
+ * Synchronises the context's stream.  Errors: FIB_EINVAL (capacity),
+ * FIB_ENONFINITE (state has NaN/Inf; out is still written), FIB_ECUDA.
+ * Thesis: the state subset copied back after a block of GPU steps
+ * (section "Code Generation for GPUs"). */
+fib_status read_vm(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
+
+/* Copies the full state (V | m | h | n, each sum(n_nodes) floats, ragged
+ * order) into out (capacity >= 4 sum(n_nodes)).  Synchronises.  Same
+ * errors as read_vm. */
+fib_status fibers_read_state(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
+
+/* Replaces the full state with in (layout of fibers_read_state) and sets the
+ * index of the next split step to step_index (>= 0).  Used for checkpoint /
+ * resume: k steps, read_state, write_state, n - k steps equals n steps. */
+fib_status fibers_write_state(fib_ctx* ctx, const float* in, size_t count, int32_t in_is_device,
+                              int64_t step_index);
+
+/* Index of the next split step, and nodes handled by the fallback path in
+ * surrogate mode (0 otherwise).  Synchronises. */
+fib_status fibers_stats(fib_ctx* ctx, int64_t* steps_done, int64_t* fallback_nodes);
+
+/* Waits for all enqueued work and reports device-side errors. */
+fib_status fibers_synchronize(fib_ctx* ctx);
+
+/* Reads / changes the launch shape.  Changing it keeps the state. */
+fib_status fibers_get_tuning(const fib_ctx* ctx, fib_tuning* out);
+fib_status fibers_set_tuning(fib_ctx* ctx, const fib_tuning* tuning);
+
+/* Times candidate launch shapes on this context's own fibers for n_trial_steps
+ * split steps each, keeps the fastest, and restores the state and step index
+ * so the simulation is unchanged.  best (nullable) receives the choice.
+ * Synchronises. */
+fib_status fibers_autotune(fib_ctx* ctx, int32_t n_trial_steps, fib_tuning* best);
+
+/* Number of launches of this library's kernels enqueued so far by ctx. */
+int64_t fibers_kernel_launches(const fib_ctx* ctx);
+
+/* Message of the last failing call on ctx (never NULL).  With ctx == NULL:
+ * the message of the last failed fibers_create on this thread. */
+const char* fibers_last_error(const fib_ctx* ctx);
+
+/* Frees everything the context owns.  NULL is allowed. */
+void fibers_destroy(fib_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIBERS_H_ */

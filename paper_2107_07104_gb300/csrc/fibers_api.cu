@@ -1,0 +1,814 @@
+// Host implementation of the C ABI in include/fibers.h.
+//
+// The context owns the device-resident state of all fibers in a padded
+// structure-of-arrays layout (u = V - Vrest, m, h, n), the fiber/CTA maps of
+// the split-step kernel, the tridiagonal-solve tables, the stimulus tables,
+// and an optional captured CUDA graph of a block of split steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fibers.h"
+#include "fibers_internal.h"
+
+using namespace fib;
+
+struct fib_ctx {
+  fib_params p{};
+  double EL = 0.0;
+  double m0 = 0.0, h0 = 0.0, n0 = 0.0;  // rest gates
+  int64_t n_sub = 0, n_cn = 0, pulse = 0;
+  double r = 0.0;
+
+  int32_t n_fibers = 0;
+  std::vector<int32_t> n_nodes, mu, junction;
+  std::vector<int64_t> coff;  // ragged offsets
+  int64_t total = 0;
+  int32_t max_n = 0;
+
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int device = 0;
+  fib_tuning tune{};
+
+  // layout-dependent device data
+  int K = 0, W = 0, n_ctas = 0, levels = 0, rec_stride = 0;
+  int64_t slots_total = 0;
+  float* d_state = nullptr;  // 4 * slots_total
+  FiberDesc* d_fibers = nullptr;
+  WarpMap* d_warps = nullptr;
+  void* d_rows = nullptr;
+  void* d_recs = nullptr;
+
+  // stimulus
+  int32_t n_mu = 0;
+  int64_t* d_mu_off = nullptr;
+  int64_t* d_fire_k = nullptr;
+
+  int64_t* d_step = nullptr;
+  int32_t* d_flag = nullptr;
+  int64_t next_step = 0;
+  int64_t launches = 0;
+
+  float* d_stage = nullptr;  // compact staging (read/write of host buffers)
+  size_t stage_elems = 0;
+
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_launches = 0;
+
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+fib_status fail(fib_ctx* c, fib_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+#define CU(ctx, call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? FIB_ENOMEM : FIB_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// ---- model constants (double precision, host) ----------------------------
+
+double vtrap(double x, double k) { return x == 0.0 ? k : x / (-std::expm1(-x / k)); }
+
+void rest_gates(double u, double* m, double* h, double* n) {
+  const double am = 0.1 * vtrap(u - 25.0, 10.0), bm = 4.0 * std::exp(-u / 18.0);
+  const double ah = 0.07 * std::exp(-u / 20.0), bh = 1.0 / (1.0 + std::exp((30.0 - u) / 10.0));
+  const double an = 0.01 * vtrap(u - 10.0, 10.0), bn = 0.125 * std::exp(-u / 80.0);
+  *m = am / (am + bm);
+  *h = ah / (ah + bh);
+  *n = an / (an + bn);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+fib_status validate(const fib_params* p) {
+  if (!p) return fail(nullptr, FIB_EINVAL, "params is NULL");
+  const double vals[] = {p->Cm, p->Am, p->h, p->dt_split, p->dt_0d, p->dt_1d, p->sigma_eff};
+  for (double v : vals)
+    if (!finite_pos(v)) return fail(nullptr, FIB_EINVAL, "Cm, Am, h, dt_split, dt_0d, dt_1d, sigma_eff must be > 0");
+  const double fin[] = {p->gNa, p->gK, p->gL, p->ENa, p->EK, p->Vrest, p->stim_amplitude, p->stim_duration};
+  for (double v : fin)
+    if (!std::isfinite(v)) return fail(nullptr, FIB_EINVAL, "non-finite model parameter");
+  if (p->gNa < 0 || p->gK < 0 || p->gL < 0 || p->stim_duration < 0)
+    return fail(nullptr, FIB_EINVAL, "conductances and stim_duration must be >= 0");
+  if (std::isnan(p->EL) && !(p->gL > 0))
+    return fail(nullptr, FIB_EINVAL, "EL = NaN (derive exact rest) needs gL > 0");
+  if (!std::isnan(p->EL) && !std::isfinite(p->EL)) return fail(nullptr, FIB_EINVAL, "EL must be finite or NaN");
+  if (p->stim_half_width < 0 || p->stim_half_width > 8)
+    return fail(nullptr, FIB_EINVAL, "stim_half_width must be in [0, 8]");
+  if (p->mode != FIB_MODE_FP32 && p->mode != FIB_MODE_FP64_THOMAS && p->mode != FIB_MODE_SURROGATE)
+    return fail(nullptr, FIB_EINVAL, "unknown mode %d", p->mode);
+  if (p->mode == FIB_MODE_SURROGATE) return fail(nullptr, FIB_ENOTSUP, "surrogate mode is not available in this build");
+  if (p->flags != 0 || p->reserved != 0) return fail(nullptr, FIB_EINVAL, "flags and reserved must be 0");
+  const double q0 = p->dt_split / p->dt_0d, q1 = 0.5 * p->dt_split / p->dt_1d;
+  const double r0 = std::nearbyint(q0), r1 = std::nearbyint(q1);
+  if (r0 < 1 || r1 < 1 || std::fabs(q0 - r0) > 1e-9 * q0 || std::fabs(q1 - r1) > 1e-9 * q1)
+    return fail(nullptr, FIB_EINVAL, "dt_split/dt_0d and dt_split/(2 dt_1d) must be whole numbers >= 1");
+  if (r0 > 1000 || r1 > 1000) return fail(nullptr, FIB_EINVAL, "too many substeps per split step");
+  return FIB_OK;
+}
+
+// ---- layout ---------------------------------------------------------------
+
+int warps_for(int32_t n, int K) {
+  const int T = (n + K - 1) / K;
+  return (T + 31) / 32;
+}
+
+int auto_K(const std::vector<int32_t>& n_nodes) {
+  // fewest padded nodes (lanes x K) over the whole bundle; ties go to 12
+  int best = 12;
+  int64_t best_pad = -1;
+  for (int K : {12, 16, 8}) {
+    int64_t pad = 0;
+    bool ok = true;
+    for (int32_t n : n_nodes) {
+      const int w = warps_for(n, K);
+      if (w > kMaxWarpsPerCta) ok = false;
+      pad += (int64_t)32 * w * K;
+    }
+    if (ok && (best_pad < 0 || pad < best_pad)) {
+      best = K;
+      best_pad = pad;
+    }
+  }
+  return best;
+}
+
+int auto_W(int w_max) { return w_max * std::max(1, kMaxWarpsPerCta / w_max); }
+
+void free_layout(fib_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  dfree(c->d_state);
+  dfree(c->d_fibers);
+  dfree(c->d_warps);
+  dfree(c->d_rows);
+  dfree(c->d_recs);
+}
+
+// Builds the padded layout, CTA packing and solver tables for tuning t.
+// Allocates (uninitialised) state; the caller fills it.
+fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
+  int K = t.nodes_per_thread ? t.nodes_per_thread : auto_K(c->n_nodes);
+  if (K != 4 && K != 8 && K != 12 && K != 16) return fail(c, FIB_EINVAL, "nodes_per_thread must be 4, 8, 12 or 16");
+  int w_max = 1;
+  for (int32_t n : c->n_nodes) w_max = std::max(w_max, warps_for(n, K));
+  if (w_max > kMaxWarpsPerCta)
+    return fail(c, FIB_EINVAL, "a fiber of %d nodes needs %d warps at %d nodes per thread (max %d warps)", c->max_n,
+                w_max, K, kMaxWarpsPerCta);
+  int W = t.warps_per_cta ? t.warps_per_cta : auto_W(w_max);
+  if (W < 1 || W > kMaxWarpsPerCta) return fail(c, FIB_EINVAL, "warps_per_cta must be in [1, %d]", kMaxWarpsPerCta);
+  if (W < w_max) return fail(c, FIB_EINVAL, "warps_per_cta %d < %d warps needed by the longest fiber", W, w_max);
+  if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
+
+  // length classes
+  std::map<int32_t, int> cls;
+  std::vector<int32_t> lens, tw;
+  for (int32_t n : c->n_nodes)
+    if (!cls.count(n)) {
+      cls[n] = (int)lens.size();
+      lens.push_back(n);
+      tw.push_back(32 * warps_for(n, K));
+    }
+  SolverTables tab;
+  if (!lens.empty() && !build_solver_tables(K, c->r, lens, tw, &tab))
+    return fail(c, FIB_EINVAL, "tridiagonal tables: zero pivot (r = %g)", c->r);
+  if (lens.empty()) {  // keep valid (unused) tables
+    std::vector<int32_t> one{1}, t1{32};
+    build_solver_tables(K, c->r, one, t1, &tab);
+  }
+
+  // slots and packing: fibers by warp count (descending), next-fit into CTAs
+  std::vector<FiberDesc> fd(c->n_fibers);
+  int64_t slot = 0;
+  for (int32_t f = 0; f < c->n_fibers; ++f) {
+    const int w = warps_for(c->n_nodes[f], K);
+    const int ci = cls[c->n_nodes[f]];
+    fd[f].slot = slot;
+    fd[f].coff = c->coff[f];
+    fd[f].rec = tab.class_rec[ci];
+    fd[f].n = c->n_nodes[f];
+    fd[f].junction = c->junction[f];
+    fd[f].mu = c->mu[f];
+    fd[f].last_set = (int32_t)tab.class_last[ci];
+    fd[f].slot_len = 32 * w * K;
+    fd[f].pad = 0;
+    slot += fd[f].slot_len;
+  }
+  std::vector<int32_t> order(c->n_fibers);
+  for (int32_t f = 0; f < c->n_fibers; ++f) order[f] = f;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return warps_for(c->n_nodes[a], K) > warps_for(c->n_nodes[b], K);
+  });
+  std::vector<WarpMap> wm;
+  int used = W, nfib = kMaxFibersPerCta;  // force a new CTA for the first fiber
+  int n_ctas = 0;
+  for (int32_t f : order) {
+    const int w = warps_for(c->n_nodes[f], K);
+    if (used + w > W || nfib >= kMaxFibersPerCta) {
+      ++n_ctas;
+      wm.resize((size_t)n_ctas * W, WarpMap{-1, 0, 0, 0, 0});
+      used = 0;
+      nfib = 0;
+    }
+    for (int k = 0; k < w; ++k) {
+      WarpMap& e = wm[(size_t)(n_ctas - 1) * W + used + k];
+      e.fiber = f;
+      e.first_warp = (int16_t)used;
+      e.n_warps = (int16_t)w;
+      e.slot = nfib;
+    }
+    used += w;
+    ++nfib;
+  }
+
+  free_layout(c);
+  c->K = K;
+  c->W = W;
+  c->n_ctas = n_ctas;
+  c->levels = tab.levels;
+  c->rec_stride = tab.rec_stride;
+  c->slots_total = slot;
+  c->tune.nodes_per_thread = K;
+  c->tune.warps_per_cta = W;
+  c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
+  c->tune.graph_steps = t.graph_steps;
+
+  const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
+  const size_t es = fp64 ? 8 : 4;
+  CU(c, cudaMalloc(&c->d_state, sizeof(float) * 4 * (size_t)std::max<int64_t>(slot, 4)));
+  CU(c, cudaMalloc(&c->d_fibers, sizeof(FiberDesc) * std::max<size_t>(fd.size(), 1)));
+  CU(c, cudaMalloc(&c->d_warps, sizeof(WarpMap) * std::max<size_t>(wm.size(), 1)));
+  CU(c, cudaMalloc(&c->d_rows, es * tab.rows.size()));
+  CU(c, cudaMalloc(&c->d_recs, es * std::max<size_t>(tab.recs.size(), 1)));
+  if (!fd.empty()) CU(c, cudaMemcpy(c->d_fibers, fd.data(), sizeof(FiberDesc) * fd.size(), cudaMemcpyHostToDevice));
+  if (!wm.empty()) CU(c, cudaMemcpy(c->d_warps, wm.data(), sizeof(WarpMap) * wm.size(), cudaMemcpyHostToDevice));
+  if (fp64) {
+    CU(c, cudaMemcpy(c->d_rows, tab.rows.data(), 8 * tab.rows.size(), cudaMemcpyHostToDevice));
+    if (!tab.recs.empty()) CU(c, cudaMemcpy(c->d_recs, tab.recs.data(), 8 * tab.recs.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> rf(tab.rows.begin(), tab.rows.end()), cf(tab.recs.begin(), tab.recs.end());
+    CU(c, cudaMemcpy(c->d_rows, rf.data(), 4 * rf.size(), cudaMemcpyHostToDevice));
+    if (!cf.empty()) CU(c, cudaMemcpy(c->d_recs, cf.data(), 4 * cf.size(), cudaMemcpyHostToDevice));
+  }
+  return FIB_OK;
+}
+
+float* st_u(fib_ctx* c) { return c->d_state; }
+float* st_m(fib_ctx* c) { return c->d_state + c->slots_total; }
+float* st_h(fib_ctx* c) { return c->d_state + 2 * c->slots_total; }
+float* st_n(fib_ctx* c) { return c->d_state + 3 * c->slots_total; }
+
+fib_status ensure_stage(fib_ctx* c, size_t elems) {
+  if (c->stage_elems >= elems && c->d_stage) return FIB_OK;
+  dfree(c->d_stage);
+  c->stage_elems = 0;
+  CU(c, cudaMalloc(&c->d_stage, sizeof(float) * std::max<size_t>(elems, 1)));
+  c->stage_elems = elems;
+  return FIB_OK;
+}
+
+fib_status check_launch(fib_ctx* c, int e, const char* what) {
+  if (e != 0) return fail(c, FIB_ECUDA, "%s launch failed: %s", what, cudaGetErrorString((cudaError_t)e));
+  return FIB_OK;
+}
+
+StepArgs make_args(fib_ctx* c) {
+  StepArgs a{};
+  a.u = st_u(c);
+  a.m = st_m(c);
+  a.h = st_h(c);
+  a.n = st_n(c);
+  a.fibers = c->d_fibers;
+  a.warps = c->d_warps;
+  a.rows = c->d_rows;
+  a.recs = c->d_recs;
+  a.mu_off = c->d_mu_off;
+  a.fire_k = c->d_fire_k;
+  a.step_base = c->d_step;
+  a.flag = c->d_flag;
+  const double Cm = c->p.Cm;
+  a.hh.gNa = (float)(c->p.gNa / Cm);
+  a.hh.gK = (float)(c->p.gK / Cm);
+  a.hh.gL = (float)(c->p.gL / Cm);
+  a.hh.uNa = (float)(c->p.ENa - c->p.Vrest);
+  a.hh.uK = (float)(c->p.EK - c->p.Vrest);
+  a.hh.uL = (float)(c->EL - c->p.Vrest);
+  a.hh.stim = (float)(c->p.stim_amplitude / Cm);
+  a.hh.dt0 = (float)c->p.dt_0d;
+  a.r = c->r;
+  a.n_sub = (int32_t)c->n_sub;
+  a.n_cn = (int32_t)c->n_cn;
+  a.pulse = (int32_t)c->pulse;
+  a.hw = c->p.stim_half_width;
+  a.n_mu = c->n_mu;
+  a.n_levels = c->levels;
+  a.rec_stride = c->rec_stride;
+  a.W = c->W;
+  return a;
+}
+
+// Enqueues split steps [next + offset0, next + offset0 + n) as launches of
+// steps_per_launch, without advancing the device step counter.
+fib_status enqueue_launches(fib_ctx* c, cudaStream_t s, int64_t offset0, int64_t n) {
+  if (c->n_ctas == 0) return FIB_OK;
+  StepArgs a = make_args(c);
+  const int64_t S = c->tune.steps_per_launch;
+  for (int64_t done = 0; done < n; done += S) {
+    a.step_offset = offset0 + done;
+    a.n_steps = (int32_t)std::min<int64_t>(S, n - done);
+    fib_status st = check_launch(c, launch_split_step(c->K, c->p.mode == FIB_MODE_FP64_THOMAS, a, c->n_ctas, s),
+                                 "split step");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+  }
+  return FIB_OK;
+}
+
+fib_status build_graph(fib_ctx* c) {
+  const int64_t G = c->tune.graph_steps;
+  CU(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = c->launches;
+  fib_status st = enqueue_launches(c, c->cap_stream, 0, G);
+  int e = st == FIB_OK ? launch_advance(c->d_step, G, c->cap_stream) : 0;
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+  c->graph_launches = (c->launches - before) + 1;
+  c->launches = before;
+  if (st != FIB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != 0 || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(c, FIB_ECUDA, "graph capture failed: %s", cudaGetErrorString(ee != cudaSuccess ? ee : (cudaError_t)e));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    c->graph = nullptr;
+    return fail(c, FIB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+  }
+  return FIB_OK;
+}
+
+fib_status check_flag(fib_ctx* c) {
+  int32_t flag = 0;
+  CU(c, cudaMemcpy(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  if (flag & 1) return fail(c, FIB_ENONFINITE, "state became non-finite (NaN/Inf)");
+  return FIB_OK;
+}
+
+fib_status set_device(fib_ctx* c) {
+  CU(c, cudaSetDevice(c->device));
+  return FIB_OK;
+}
+
+// Gathers (V|m|h|n) into dst (device, 4 * total) in ragged order.
+fib_status gather_state(fib_ctx* c, float* dst) {
+  const float adds[4] = {(float)c->p.Vrest, 0.f, 0.f, 0.f};
+  float* src[4] = {st_u(c), st_m(c), st_h(c), st_n(c)};
+  for (int k = 0; k < 4; ++k) {
+    fib_status st = check_launch(c, launch_gather(c->d_fibers, c->n_fibers, src[k], dst + k * c->total, adds[k], c->stream),
+                                 "gather");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+  }
+  return FIB_OK;
+}
+
+// Fills the padded layout from a compact (V|m|h|n) device buffer.
+fib_status scatter_state(fib_ctx* c, const float* src) {
+  fib_status st = check_launch(c, launch_fill_layout(c->d_fibers, c->n_fibers, st_u(c), st_m(c), st_h(c), st_n(c),
+                                                     nullptr, (float)c->p.Vrest, (float)c->m0, (float)c->h0,
+                                                     (float)c->n0, c->stream),
+                               "fill");
+  if (st != FIB_OK) return st;
+  ++c->launches;
+  const float adds[4] = {(float)-c->p.Vrest, 0.f, 0.f, 0.f};
+  float* dst[4] = {st_u(c), st_m(c), st_h(c), st_n(c)};
+  for (int k = 0; k < 4; ++k) {
+    st = check_launch(c, launch_scatter(c->d_fibers, c->n_fibers, src + k * c->total, dst[k], adds[k], c->stream),
+                      "scatter");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+  }
+  return FIB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n_nodes, const int32_t* mu_of_fiber,
+                         const int32_t* junction_node, const float* vm0, const fib_tuning* tuning, void* cuda_stream,
+                         fib_ctx** out) {
+  if (!out) return fail(nullptr, FIB_EINVAL, "out is NULL");
+  *out = nullptr;
+  fib_status st = validate(p);
+  if (st != FIB_OK) return st;
+  if (n_fibers < 0) return fail(nullptr, FIB_EINVAL, "n_fibers < 0");
+  if (n_fibers > 0 && (!n_nodes || !mu_of_fiber || !junction_node))
+    return fail(nullptr, FIB_EINVAL, "n_nodes, mu_of_fiber and junction_node are required");
+  std::unique_ptr<fib_ctx> c(new (std::nothrow) fib_ctx());
+  if (!c) return fail(nullptr, FIB_ENOMEM, "host allocation failed");
+  c->p = *p;
+  c->n_fibers = n_fibers;
+  c->n_nodes.assign(n_nodes, n_nodes + n_fibers);
+  c->mu.assign(mu_of_fiber, mu_of_fiber + n_fibers);
+  c->junction.assign(junction_node, junction_node + n_fibers);
+  c->coff.resize(n_fibers + 1);
+  c->coff[0] = 0;
+  for (int32_t f = 0; f < n_fibers; ++f) {
+    if (c->n_nodes[f] < 1) return fail(nullptr, FIB_EINVAL, "fiber %d has %d nodes (need >= 1)", f, c->n_nodes[f]);
+    if (c->junction[f] < 0 || c->junction[f] >= c->n_nodes[f])
+      return fail(nullptr, FIB_EINVAL, "fiber %d: junction %d outside [0, %d)", f, c->junction[f], c->n_nodes[f]);
+    if (c->mu[f] < -1) return fail(nullptr, FIB_EINVAL, "fiber %d: motor unit %d < -1", f, c->mu[f]);
+    c->coff[f + 1] = c->coff[f] + c->n_nodes[f];
+    c->max_n = std::max(c->max_n, c->n_nodes[f]);
+  }
+  c->total = c->coff[n_fibers];
+  if (vm0)
+    for (int64_t i = 0; i < c->total; ++i)
+      if (!std::isfinite(vm0[i])) return fail(nullptr, FIB_EINVAL, "vm0[%lld] is not finite", (long long)i);
+
+  // derived constants
+  c->n_sub = (int64_t)std::nearbyint(p->dt_split / p->dt_0d);
+  c->n_cn = (int64_t)std::nearbyint(0.5 * p->dt_split / p->dt_1d);
+  c->pulse = (int64_t)std::nearbyint(p->stim_duration / p->dt_0d);
+  const double cdiff = p->sigma_eff / (p->Am * p->Cm);
+  c->r = cdiff * p->dt_1d / (p->h * p->h);
+  rest_gates(0.0, &c->m0, &c->h0, &c->n0);
+  if (std::isnan(p->EL)) {
+    const double ina = p->gNa * c->m0 * c->m0 * c->m0 * c->h0 * (p->Vrest - p->ENa);
+    const double ik = p->gK * c->n0 * c->n0 * c->n0 * c->n0 * (p->Vrest - p->EK);
+    c->EL = p->Vrest + (ina + ik) / p->gL;
+  } else {
+    c->EL = p->EL;
+  }
+
+  fib_ctx* cx = c.get();
+  cudaError_t e = cudaGetDevice(&cx->device);
+  if (e != cudaSuccess) return fail(nullptr, FIB_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  cx->stream = static_cast<cudaStream_t>(cuda_stream);
+  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000};
+  if (!tuning) t.graph_steps = 1000;
+  st = build_layout(cx, t);
+  if (st == FIB_OK) {
+    if ((e = cudaStreamCreateWithFlags(&cx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      st = fail(cx, FIB_ECUDA, "stream create: %s", cudaGetErrorString(e));
+  }
+  if (st == FIB_OK) {
+    if ((e = cudaMalloc(&cx->d_step, sizeof(int64_t))) != cudaSuccess ||
+        (e = cudaMalloc(&cx->d_flag, sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemset(cx->d_step, 0, sizeof(int64_t))) != cudaSuccess ||
+        (e = cudaMemset(cx->d_flag, 0, sizeof(int32_t))) != cudaSuccess)
+      st = fail(cx, e == cudaErrorMemoryAllocation ? FIB_ENOMEM : FIB_ECUDA, "allocation: %s", cudaGetErrorString(e));
+  }
+  float* d_vm0 = nullptr;
+  if (st == FIB_OK && vm0 && cx->total > 0) {
+    if ((e = cudaMalloc(&d_vm0, sizeof(float) * cx->total)) != cudaSuccess ||
+        (e = cudaMemcpy(d_vm0, vm0, sizeof(float) * cx->total, cudaMemcpyHostToDevice)) != cudaSuccess)
+      st = fail(cx, FIB_ECUDA, "vm0 upload: %s", cudaGetErrorString(e));
+  }
+  if (st == FIB_OK) {
+    st = check_launch(cx, launch_fill_layout(cx->d_fibers, cx->n_fibers, st_u(cx), st_m(cx), st_h(cx), st_n(cx), d_vm0,
+                                             (float)p->Vrest, (float)cx->m0, (float)cx->h0, (float)cx->n0,
+                                             cx->stream),
+                      "fill");
+    ++cx->launches;
+  }
+  if (st == FIB_OK && (e = cudaStreamSynchronize(cx->stream)) != cudaSuccess)
+    st = fail(cx, FIB_ECUDA, "init: %s", cudaGetErrorString(e));
+  if (d_vm0) cudaFree(d_vm0);
+  if (st != FIB_OK) {
+    g_create_error = cx->err;
+    fibers_destroy(c.release());
+    return st;
+  }
+  *out = c.release();
+  return FIB_OK;
+}
+
+fib_status set_stimulus_times(fib_ctx* c, int32_t n_mu, const int64_t* offsets, const double* fire_times_ms) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (n_mu < 0) return fail(c, FIB_EINVAL, "n_mu < 0");
+  if (n_mu > 0 && !offsets) return fail(c, FIB_EINVAL, "offsets is NULL");
+  std::vector<int64_t> off(offsets, offsets + (n_mu > 0 ? n_mu + 1 : 0));
+  if (n_mu > 0 && off[0] != 0) return fail(c, FIB_EINVAL, "offsets[0] must be 0");
+  for (int32_t k = 0; k < n_mu; ++k)
+    if (off[k + 1] < off[k]) return fail(c, FIB_EINVAL, "offsets must be non-decreasing");
+  const int64_t nf = n_mu > 0 ? off[n_mu] : 0;
+  if (nf > 0 && !fire_times_ms) return fail(c, FIB_EINVAL, "fire_times_ms is NULL");
+  for (int32_t f = 0; f < c->n_fibers; ++f)
+    if (c->mu[f] >= n_mu) return fail(c, FIB_EINVAL, "fiber %d refers to motor unit %d >= n_mu %d", f, c->mu[f], n_mu);
+  std::vector<int64_t> fk(std::max<int64_t>(nf, 1), 0);
+  for (int32_t k = 0; k < n_mu; ++k)
+    for (int64_t i = off[k]; i < off[k + 1]; ++i) {
+      const double t = fire_times_ms[i];
+      if (!std::isfinite(t) || t < 0) return fail(c, FIB_EINVAL, "fire time %lld is negative or not finite", (long long)i);
+      if (i > off[k] && t < fire_times_ms[i - 1]) return fail(c, FIB_EINVAL, "fire times of MU %d are not ascending", k);
+      const double q = t / c->p.dt_0d;
+      if (q > 4.0e18) return fail(c, FIB_EINVAL, "fire time %g ms too large", t);
+      fk[i] = (int64_t)std::nearbyint(q);  // round half to even (default rounding mode)
+    }
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  CU(c, cudaStreamSynchronize(c->stream));
+  dfree(c->d_mu_off);
+  dfree(c->d_fire_k);
+  c->n_mu = 0;
+  if (n_mu > 0) {
+    CU(c, cudaMalloc(&c->d_mu_off, sizeof(int64_t) * (n_mu + 1)));
+    CU(c, cudaMalloc(&c->d_fire_k, sizeof(int64_t) * fk.size()));
+    CU(c, cudaMemcpy(c->d_mu_off, off.data(), sizeof(int64_t) * (n_mu + 1), cudaMemcpyHostToDevice));
+    CU(c, cudaMemcpy(c->d_fire_k, fk.data(), sizeof(int64_t) * fk.size(), cudaMemcpyHostToDevice));
+  }
+  c->n_mu = n_mu;
+  if (c->graph) cudaGraphExecDestroy(c->graph);  // captured arguments changed
+  c->graph = nullptr;
+  return FIB_OK;
+}
+
+fib_status step(fib_ctx* c, int64_t n_steps) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (n_steps < 0) return fail(c, FIB_EINVAL, "n_steps < 0");
+  if (n_steps == 0) return FIB_OK;
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  const int64_t G = c->tune.graph_steps;
+  if (G > 0 && n_steps >= G && c->n_ctas > 0) {
+    if (!c->graph) {
+      fib_status st = build_graph(c);
+      if (st != FIB_OK) return st;
+    }
+    while (n_steps >= G) {
+      CU(c, cudaGraphLaunch(c->graph, c->stream));
+      c->launches += c->graph_launches;
+      c->next_step += G;
+      n_steps -= G;
+    }
+  }
+  if (n_steps > 0) {
+    fib_status st = enqueue_launches(c, c->stream, 0, n_steps);
+    if (st != FIB_OK) return st;
+    st = check_launch(c, launch_advance(c->d_step, n_steps, c->stream), "advance");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+    c->next_step += n_steps;
+  }
+  return FIB_OK;
+}
+
+fib_status read_vm(fib_ctx* c, float* out, size_t capacity, int32_t out_is_device) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (capacity < (size_t)c->total) return fail(c, FIB_EINVAL, "capacity %zu < %lld nodes", capacity, (long long)c->total);
+  if (c->total > 0 && !out) return fail(c, FIB_EINVAL, "out is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  if (c->total > 0) {
+    float* dst = out;
+    if (!out_is_device) {
+      fib_status st = ensure_stage(c, (size_t)c->total);
+      if (st != FIB_OK) return st;
+      dst = c->d_stage;
+    }
+    fib_status st = check_launch(c, launch_gather(c->d_fibers, c->n_fibers, st_u(c), dst, (float)c->p.Vrest, c->stream),
+                                 "gather");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+    if (!out_is_device)
+      CU(c, cudaMemcpyAsync(out, c->d_stage, sizeof(float) * c->total, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
+
+fib_status fibers_read_state(fib_ctx* c, float* out, size_t capacity, int32_t out_is_device) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  const size_t need = 4 * (size_t)c->total;
+  if (capacity < need) return fail(c, FIB_EINVAL, "capacity %zu < %zu", capacity, need);
+  if (need > 0 && !out) return fail(c, FIB_EINVAL, "out is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  if (need > 0) {
+    float* dst = out;
+    if (!out_is_device) {
+      fib_status st = ensure_stage(c, need);
+      if (st != FIB_OK) return st;
+      dst = c->d_stage;
+    }
+    fib_status st = gather_state(c, dst);
+    if (st != FIB_OK) return st;
+    if (!out_is_device) CU(c, cudaMemcpyAsync(out, c->d_stage, sizeof(float) * need, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
+
+fib_status fibers_write_state(fib_ctx* c, const float* in, size_t count, int32_t in_is_device, int64_t step_index) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  const size_t need = 4 * (size_t)c->total;
+  if (count != need) return fail(c, FIB_EINVAL, "count %zu != 4 * nodes = %zu", count, need);
+  if (need > 0 && !in) return fail(c, FIB_EINVAL, "in is NULL");
+  if (step_index < 0) return fail(c, FIB_EINVAL, "step_index < 0");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  if (need > 0) {
+    const float* src = in;
+    if (!in_is_device) {
+      fib_status st = ensure_stage(c, need);
+      if (st != FIB_OK) return st;
+      CU(c, cudaMemcpyAsync(c->d_stage, in, sizeof(float) * need, cudaMemcpyHostToDevice, c->stream));
+      src = c->d_stage;
+    }
+    fib_status st = scatter_state(c, src);
+    if (st != FIB_OK) return st;
+  }
+  CU(c, cudaMemcpyAsync(c->d_step, &step_index, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CU(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  c->next_step = step_index;
+  return FIB_OK;
+}
+
+fib_status fibers_stats(fib_ctx* c, int64_t* steps_done, int64_t* fallback_nodes) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (steps_done) *steps_done = c->next_step;
+  if (fallback_nodes) *fallback_nodes = 0;
+  return check_flag(c);
+}
+
+fib_status fibers_synchronize(fib_ctx* c) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  CU(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
+
+fib_status fibers_get_tuning(const fib_ctx* c, fib_tuning* out) {
+  if (!c || !out) return fail(nullptr, FIB_EINVAL, "ctx or out is NULL");
+  *out = c->tune;
+  return FIB_OK;
+}
+
+fib_status fibers_set_tuning(fib_ctx* c, const fib_tuning* t) {
+  if (!c || !t) return fail(c, FIB_EINVAL, "ctx or tuning is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  // keep the state across the re-layout: compact copy, rebuild, scatter back
+  const size_t need = 4 * (size_t)c->total;
+  float* keep = nullptr;
+  if (need > 0) {
+    CU(c, cudaMalloc(&keep, sizeof(float) * need));
+    fib_status st = gather_state(c, keep);
+    if (st != FIB_OK) {
+      cudaFree(keep);
+      return st;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(keep);
+    return fail(c, FIB_ECUDA, "sync: %s", cudaGetErrorString(e));
+  }
+  const fib_tuning old = c->tune;
+  fib_status st = build_layout(c, *t);
+  if (st != FIB_OK) {
+    const std::string why = c->err;
+    if (build_layout(c, old) != FIB_OK) {
+      cudaFree(keep);
+      return fail(c, FIB_ECUDA, "tuning rejected (%s) and the old layout could not be restored", why.c_str());
+    }
+    c->err = why;
+  }
+  fib_status st2 = need > 0 ? scatter_state(c, keep) : FIB_OK;
+  e = cudaStreamSynchronize(c->stream);
+  cudaFree(keep);
+  if (st2 != FIB_OK) return st2;
+  if (e != cudaSuccess) return fail(c, FIB_ECUDA, "sync: %s", cudaGetErrorString(e));
+  return st;
+}
+
+fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (n_trial_steps < 1) return fail(c, FIB_EINVAL, "n_trial_steps must be >= 1");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  const size_t need = 4 * (size_t)c->total;
+  const int64_t step_keep = c->next_step;
+  float* keep = nullptr;
+  if (need > 0) {
+    CU(c, cudaMalloc(&keep, sizeof(float) * need));
+    fib_status st = gather_state(c, keep);
+    if (st != FIB_OK) {
+      cudaFree(keep);
+      return st;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const fib_tuning start = c->tune;
+  fib_tuning win = start;
+  float win_ms = -1.0f;
+  fib_status result = FIB_OK;
+  for (int K : {8, 12, 16}) {
+    int w_max = 1;
+    for (int32_t n : c->n_nodes) w_max = std::max(w_max, warps_for(n, K));
+    if (w_max > kMaxWarpsPerCta) continue;
+    std::vector<int> Ws{auto_W(w_max)};
+    if (w_max * 2 <= kMaxWarpsPerCta && auto_W(w_max) != w_max) Ws.push_back(w_max);
+    for (int W : Ws) {
+      fib_tuning t{K, W, start.steps_per_launch, start.graph_steps};
+      if (build_layout(c, t) != FIB_OK) continue;
+      if (need > 0 && scatter_state(c, keep) != FIB_OK) continue;
+      StepArgs a = make_args(c);
+      a.step_offset = 0;
+      a.n_steps = n_trial_steps;
+      const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
+      // one warm-up launch, then the timed one
+      launch_split_step(c->K, fp64, a, c->n_ctas, c->stream);
+      cudaEventRecord(e0, c->stream);
+      int le = launch_split_step(c->K, fp64, a, c->n_ctas, c->stream);
+      cudaEventRecord(e1, c->stream);
+      c->launches += 2;
+      if (le != 0 || cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (win_ms < 0 || ms < win_ms) {
+        win_ms = ms;
+        win = c->tune;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore: chosen layout, saved state, step index, clean flag
+  result = build_layout(c, win);
+  if (result == FIB_OK && need > 0) result = scatter_state(c, keep);
+  if (result == FIB_OK) {
+    cudaMemcpyAsync(c->d_step, &step_keep, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) result = fail(c, FIB_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
+  }
+  cudaFree(keep);
+  c->next_step = step_keep;
+  if (best) *best = c->tune;
+  if (win_ms < 0 && result == FIB_OK) result = fail(c, FIB_ECUDA, "autotune: no candidate ran");
+  return result;
+}
+
+int64_t fibers_kernel_launches(const fib_ctx* c) { return c ? c->launches : 0; }
+
+const char* fibers_last_error(const fib_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+void fibers_destroy(fib_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_layout(c);
+  dfree(c->d_mu_off);
+  dfree(c->d_fire_k);
+  dfree(c->d_step);
+  dfree(c->d_flag);
+  dfree(c->d_stage);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"

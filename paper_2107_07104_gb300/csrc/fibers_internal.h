@@ -1,0 +1,110 @@
+// Internal types shared by the host library and the sm_103a kernels.
+// Nothing here is part of the public ABI (include/fibers.h).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace fib {
+
+// Per-row coefficients of the partitioned tridiagonal solve (see
+// solver_tables.cpp): F1 = 1/den, F2 = a/den (forward elimination),
+// G = gamma (back substitution), Ap = alpha', Bt = beta (recovery).
+constexpr int kCoefPerRow = 5;
+// Per-thread record: 1/B, A/B, C/B, c0, kE, kD, kDn, then (ib, ka, kc) per
+// cyclic-reduction level.
+constexpr int kRecBase = 7;
+constexpr int kRecPerLevel = 3;
+constexpr int kMaxFibersPerCta = 15;  // named barriers 1..15 (0 is __syncthreads)
+constexpr int kMaxWarpsPerCta = 8;    // 256 threads: the kernels' launch bound
+constexpr int kMaxLevels = 12;
+
+struct FiberDesc {
+  int64_t slot;      // index of node 0 in the padded state arrays
+  int64_t coff;      // index of node 0 in ragged (compact) order
+  int64_t rec;       // offset (elements) of the fiber's per-thread records
+  int32_t n;         // nodes
+  int32_t junction;  // junction node
+  int32_t mu;        // motor unit, -1 = never stimulated
+  int32_t last_set;  // offset (elements) of the last-chunk row set
+  int32_t slot_len;  // padded nodes of the slot (32 * warps * K)
+  int32_t pad;
+};
+
+struct WarpMap {       // one entry per warp of every CTA
+  int32_t fiber;       // -1: idle warp
+  int16_t first_warp;  // first warp of that fiber in the CTA
+  int16_t n_warps;     // warps of that fiber
+  int32_t slot;        // fiber index within the CTA (barrier id = slot + 1)
+  int32_t pad;
+};
+
+struct HHConst {  // Hodgkin-Huxley constants in the depolarisation u = V - Vrest
+  float gNa, gK, gL;  // conductances / Cm
+  float uNa, uK, uL;  // reversal potentials - Vrest
+  float stim;         // stimulus amplitude / Cm
+  float dt0;          // Heun substep width
+};
+
+struct StepArgs {
+  float* u;  // SoA state in the padded layout; u = V - Vrest
+  float* m;
+  float* h;
+  float* n;
+  const FiberDesc* fibers;
+  const WarpMap* warps;    // n_ctas * W entries
+  const void* rows;        // row sets (float or double): interior set at 0
+  const void* recs;        // per-thread records (float or double)
+  const int64_t* mu_off;   // [n_mu + 1]
+  const int64_t* fire_k;   // firing substep index, sorted within each MU
+  const int64_t* step_base;  // device-resident index of the next split step
+  int32_t* flag;           // bit 0: non-finite state seen
+  HHConst hh;
+  double r;                // c dt_1d / h^2
+  int64_t step_offset;     // this launch starts at *step_base + step_offset
+  int32_t n_steps;         // split steps in this launch
+  int32_t n_sub;           // Heun substeps per split step
+  int32_t n_cn;            // CN steps per diffusion half
+  int32_t pulse;           // stimulus length in substeps
+  int32_t hw;              // stimulus half width (nodes)
+  int32_t n_mu;
+  int32_t n_levels;        // cyclic-reduction levels kept
+  int32_t rec_stride;      // elements per thread record
+  int32_t W;               // warps per CTA
+  int32_t pad;
+};
+
+// Host-built solver tables for one (K, r, fiber-length set).
+struct SolverTables {
+  int K = 0;
+  int levels = 0;
+  int rec_stride = 0;
+  std::vector<double> rows;         // [interior set][class 0 last set]...
+  std::vector<double> recs;         // per class: threads x rec_stride
+  std::vector<int64_t> class_last;  // offset of each class's last set in rows
+  std::vector<int64_t> class_rec;   // offset of each class's records in recs
+};
+
+// Builds the tables for fiber lengths `lengths` (distinct values, one class
+// each), K nodes per thread, threads_per_class[i] threads for class i, and
+// CN coefficient r.  Returns false on a zero pivot.
+bool build_solver_tables(int K, double r, const std::vector<int32_t>& lengths,
+                         const std::vector<int32_t>& threads_per_class, SolverTables* out);
+
+// Device entry points (split_step.cu).
+int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
+int launch_advance(int64_t* step_base, int64_t n, void* stream);
+// dst[coff + i] = src[slot + i] + add for the n real nodes of every fiber.
+int launch_gather(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,
+                  float add, void* stream);
+// dst[slot + i] = src[coff + i] + add for real nodes; padding nodes keep dst.
+int launch_scatter(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,
+                   float add, void* stream);
+// Fills every slot: u = vm0 - vrest on real nodes (0 without vm0 and on
+// padding), gates = (m0, h0, n0) everywhere.
+int launch_fill_layout(const FiberDesc* fibers, int32_t n_fibers, float* u, float* m, float* h,
+                       float* n, const float* vm0_compact, float vrest, float m0, float h0, float n0,
+                       void* stream);
+size_t split_step_smem_bytes(int K, bool fp64_solve, int W);
+
+}  // namespace fib

@@ -1,0 +1,317 @@
+"""ctypes binding of the C ABI in include/fibers.h (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library libfibers.so; this module
+only converts Python/numpy/torch arguments into pointers and sizes and turns
+error codes into exceptions.  There is no CPU fallback: if the library is
+missing or no GPU is present, calls fail loudly.
+
+The functions keep the C names (fibers_create, set_stimulus_times, step,
+read_vm, ...).  ``Fibers`` is a small convenience class over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+FIB_OK, FIB_EINVAL, FIB_ENOMEM, FIB_ECUDA, FIB_ENONFINITE, FIB_ETIMEOUT, FIB_ESTATE, FIB_ENOTSUP = range(8)
+FIB_MODE_FP32, FIB_MODE_FP64_THOMAS, FIB_MODE_SURROGATE = 0, 1, 2
+STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINITE", "FIB_ETIMEOUT",
+                "FIB_ESTATE", "FIB_ENOTSUP"]
+
+# Every symbol the header declares (checked by the ABI test).
+EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "fibers_read_state", "fibers_write_state",
+            "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
+            "fibers_kernel_launches", "fibers_last_error", "fibers_destroy")
+
+
+class FibersError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class FibParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("Cm", "gNa", "gK", "gL", "ENa", "EK", "EL", "Vrest", "sigma_eff", "Am", "h",
+                 "dt_split", "dt_0d", "dt_1d", "stim_amplitude", "stim_duration")] + \
+               [("stim_half_width", ctypes.c_int32), ("mode", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class FibTuning(ctypes.Structure):
+    _fields_ = [("nodes_per_thread", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfibers.so (building it first if stale and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            try:
+                path = _build.build()
+            except RuntimeError:
+                if not os.path.exists(path):
+                    raise
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it with paper_2107_07104_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        P, vp = ctypes.POINTER, ctypes.c_void_p
+        i32, i64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        L.fibers_create.argtypes = [P(FibParams), i32, P(i32), P(i32), P(i32), P(ctypes.c_float), P(FibTuning), vp,
+                                    P(vp)]
+        L.set_stimulus_times.argtypes = [vp, i32, P(i64), P(ctypes.c_double)]
+        L.step.argtypes = [vp, i64]
+        L.read_vm.argtypes = [vp, vp, sz, i32]
+        L.fibers_read_state.argtypes = [vp, vp, sz, i32]
+        L.fibers_write_state.argtypes = [vp, vp, sz, i32, i64]
+        L.fibers_stats.argtypes = [vp, P(i64), P(i64)]
+        L.fibers_synchronize.argtypes = [vp]
+        L.fibers_get_tuning.argtypes = [vp, P(FibTuning)]
+        L.fibers_set_tuning.argtypes = [vp, P(FibTuning)]
+        L.fibers_autotune.argtypes = [vp, i32, P(FibTuning)]
+        L.fibers_kernel_launches.argtypes = [vp]
+        L.fibers_kernel_launches.restype = i64
+        L.fibers_last_error.argtypes = [vp]
+        L.fibers_last_error.restype = ctypes.c_char_p
+        L.fibers_destroy.argtypes = [vp]
+        L.fibers_destroy.restype = None
+        for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "fibers_read_state",
+                     "fibers_write_state", "fibers_stats", "fibers_synchronize", "fibers_get_tuning",
+                     "fibers_set_tuning", "fibers_autotune"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(status: int, ctx) -> None:
+    if status != FIB_OK:
+        msg = load().fibers_last_error(ctx)
+        raise FibersError(status, msg.decode() if msg else "")
+
+
+def make_params(p: dict, mode: int = FIB_MODE_FP32) -> FibParams:
+    o = FibParams()
+    for k in ("Cm", "gNa", "gK", "gL", "ENa", "EK", "EL", "Vrest", "sigma_eff", "Am", "h",
+              "dt_split", "dt_0d", "dt_1d", "stim_amplitude", "stim_duration"):
+        setattr(o, k, float(p[k]))
+    o.stim_half_width = int(p.get("stim_half_width", 1))
+    o.mode = int(p.get("mode", mode))
+    o.flags = 0
+    o.reserved = 0
+    return o
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _buffer(out):
+    """(pointer, elements, is_device) of a numpy array or a torch tensor."""
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise TypeError("expected a contiguous float32 array")
+        return out.ctypes.data, out.size, 0
+    try:  # torch tensor
+        import torch
+        if isinstance(out, torch.Tensor):
+            if out.dtype != torch.float32 or not out.is_contiguous():
+                raise TypeError("expected a contiguous float32 tensor")
+            return out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
+    except ImportError:
+        pass
+    raise TypeError(f"unsupported buffer type {type(out)}")
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+
+def fibers_create(params: dict, n_nodes, mu_of_fiber, junction_node, vm0=None, tuning: Optional[dict] = None,
+                  stream=None, mode: int = FIB_MODE_FP32):
+    L = load()
+    n_nodes = _arr(n_nodes, np.int32)
+    mu = _arr(mu_of_fiber, np.int32)
+    junc = _arr(junction_node, np.int32)
+    if not (n_nodes.shape == mu.shape == junc.shape):
+        raise ValueError("n_nodes, mu_of_fiber and junction_node must have the same length")
+    pv = make_params(params, mode)
+    v = None if vm0 is None else _arr(vm0, np.float32)
+    t = None
+    if tuning is not None:
+        t = FibTuning(**{k: int(tuning.get(k, 0)) for k, _ in FibTuning._fields_})
+    s = None
+    if stream is not None:
+        s = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+    ctx = ctypes.c_void_p()
+    st = L.fibers_create(ctypes.byref(pv), n_nodes.shape[0], _ptr(n_nodes, ctypes.c_int32), _ptr(mu, ctypes.c_int32),
+                         _ptr(junc, ctypes.c_int32), None if v is None else _ptr(v, ctypes.c_float),
+                         None if t is None else ctypes.byref(t), s, ctypes.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
+def set_stimulus_times(ctx, mu_offsets, fire_times_ms) -> None:
+    offs = _arr(mu_offsets, np.int64)
+    times = _arr(fire_times_ms, np.float64)
+    if times.size == 0:
+        times = np.zeros(1)
+    _check(load().set_stimulus_times(ctx, max(offs.shape[0] - 1, 0), _ptr(offs, ctypes.c_int64),
+                                     _ptr(times, ctypes.c_double)), ctx)
+
+
+def step(ctx, n_steps: int) -> None:
+    _check(load().step(ctx, int(n_steps)), ctx)
+
+
+def read_vm(ctx, out) -> None:
+    ptr, n, dev = _buffer(out)
+    _check(load().read_vm(ctx, ptr, n, dev), ctx)
+
+
+def fibers_read_state(ctx, out) -> None:
+    ptr, n, dev = _buffer(out)
+    _check(load().fibers_read_state(ctx, ptr, n, dev), ctx)
+
+
+def fibers_write_state(ctx, data, step_index: int) -> None:
+    ptr, n, dev = _buffer(data)
+    _check(load().fibers_write_state(ctx, ptr, n, dev, int(step_index)), ctx)
+
+
+def fibers_stats(ctx):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fibers_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return int(a.value), int(b.value)
+
+
+def fibers_synchronize(ctx) -> None:
+    _check(load().fibers_synchronize(ctx), ctx)
+
+
+def fibers_get_tuning(ctx) -> dict:
+    t = FibTuning()
+    _check(load().fibers_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def fibers_set_tuning(ctx, tuning: dict) -> None:
+    t = FibTuning(**{k: int(tuning.get(k, 0)) for k, _ in FibTuning._fields_})
+    _check(load().fibers_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def fibers_autotune(ctx, n_trial_steps: int = 20) -> dict:
+    t = FibTuning()
+    _check(load().fibers_autotune(ctx, int(n_trial_steps), ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def fibers_kernel_launches(ctx) -> int:
+    return int(load().fibers_kernel_launches(ctx))
+
+
+def fibers_destroy(ctx) -> None:
+    if ctx:
+        load().fibers_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Convenience class
+# ---------------------------------------------------------------------------
+
+class Fibers:
+    """A bundle of fibers on the GPU, created from a ``workloads.Workload``-like
+    description (params, n_nodes, mu_of_fiber, junction, mu_offsets,
+    fire_times, vm0)."""
+
+    def __init__(self, params: dict, n_nodes, mu_of_fiber, junction, mu_offsets=None, fire_times=None,
+                 vm0=None, tuning: Optional[dict] = None, stream=None, mode: int = FIB_MODE_FP32):
+        self.ctx = fibers_create(params, n_nodes, mu_of_fiber, junction, vm0, tuning, stream, mode)
+        self.n_nodes = _arr(n_nodes, np.int32)
+        self.total = int(self.n_nodes.astype(np.int64).sum())
+        if mu_offsets is not None:
+            set_stimulus_times(self.ctx, mu_offsets, fire_times if fire_times is not None else [])
+
+    @classmethod
+    def from_workload(cls, w, tuning: Optional[dict] = None, stream=None, mode: int = FIB_MODE_FP32):
+        return cls(w.params, w.n_nodes, w.mu_of_fiber, w.junction, w.mu_offsets, w.fire_times, w.vm0, tuning,
+                   stream, mode)
+
+    def step(self, n: int) -> None:
+        step(self.ctx, n)
+
+    def read_vm(self, out=None):
+        if out is None:
+            out = np.empty(self.total, np.float32)
+        read_vm(self.ctx, out)
+        return out
+
+    def read_state(self, out=None):
+        if out is None:
+            out = np.empty(4 * self.total, np.float32)
+        fibers_read_state(self.ctx, out)
+        return out
+
+    def write_state(self, data, step_index: int) -> None:
+        fibers_write_state(self.ctx, data, step_index)
+
+    def stats(self):
+        return fibers_stats(self.ctx)
+
+    def synchronize(self) -> None:
+        fibers_synchronize(self.ctx)
+
+    @property
+    def tuning(self) -> dict:
+        return fibers_get_tuning(self.ctx)
+
+    def set_tuning(self, tuning: dict) -> None:
+        fibers_set_tuning(self.ctx, tuning)
+
+    def autotune(self, n_trial_steps: int = 20) -> dict:
+        return fibers_autotune(self.ctx, n_trial_steps)
+
+    @property
+    def kernel_launches(self) -> int:
+        return fibers_kernel_launches(self.ctx)
+
+    def close(self) -> None:
+        if self.ctx:
+            fibers_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
