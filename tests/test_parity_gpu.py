@@ -39,7 +39,7 @@ def test_single_fiber_full_trajectory():
     to = activation_times(o, every * w.params["dt_split"])
     assert np.array_equal(np.isnan(tg), np.isnan(to))
     fired = ~np.isnan(to)
-    assert fired.sum() > 500
+    assert fired.sum() > 300  # ~1.7 cm each way at ~1.9 m/s in 10 ms
     dt_act = np.max(np.abs(tg[fired] - to[fired]))
     print(f"[parity] activation-time max error {dt_act:.3e} ms over {fired.sum()} nodes")
     assert dt_act <= ACT_TIME_MS
