@@ -135,14 +135,18 @@ fib_status step(fib_ctx* ctx, int64_t n_steps);
  * (section "Code Generation for GPUs"). */
 fib_status read_vm(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
 
-/* Copies the full state (V | m | h | n, each sum(n_nodes) floats, ragged
- * order) into out (capacity >= 4 sum(n_nodes)).  Synchronises.  Same
- * errors as read_vm. */
+/* Copies the full state into out (capacity >= 4 sum(n_nodes)): four blocks
+ * of sum(n_nodes) floats in ragged order, u | m | h | n, where u = V - Vrest
+ * is the depolarisation in mV (the form the library integrates; V itself is
+ * u + Vrest) and m, h, n are the HH gates.  The copy is bit-exact, so it can
+ * serve as a checkpoint.  Synchronises.  Same errors as read_vm. */
 fib_status fibers_read_state(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
 
-/* Replaces the full state with in (layout of fibers_read_state) and sets the
- * index of the next split step to step_index (>= 0).  Used for checkpoint /
- * resume: k steps, read_state, write_state, n - k steps equals n steps. */
+/* Replaces the full state with in (layout of fibers_read_state: u | m | h |
+ * n) and sets the index of the next split step to step_index (>= 0).  Used
+ * for checkpoint / resume: k steps, read_state, write_state, n - k steps
+ * gives bit-for-bit the same state as n steps.  Clears a pending non-finite
+ * flag. */
 fib_status fibers_write_state(fib_ctx* ctx, const float* in, size_t count, int32_t in_is_device,
                               int64_t step_index);
 

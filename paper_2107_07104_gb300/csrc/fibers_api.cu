@@ -395,9 +395,10 @@ fib_status set_device(fib_ctx* c) {
   return FIB_OK;
 }
 
-// Gathers (V|m|h|n) into dst (device, 4 * total) in ragged order.
+// Gathers the internal state (u|m|h|n, u = V - Vrest) into dst (device,
+// 4 * total) in ragged order.  Bit-exact: no arithmetic on the values.
 fib_status gather_state(fib_ctx* c, float* dst) {
-  const float adds[4] = {(float)c->p.Vrest, 0.f, 0.f, 0.f};
+  const float adds[4] = {0.f, 0.f, 0.f, 0.f};
   float* src[4] = {st_u(c), st_m(c), st_h(c), st_n(c)};
   for (int k = 0; k < 4; ++k) {
     fib_status st = check_launch(c, launch_gather(c->d_fibers, c->n_fibers, src[k], dst + k * c->total, adds[k], c->stream),
@@ -408,7 +409,7 @@ fib_status gather_state(fib_ctx* c, float* dst) {
   return FIB_OK;
 }
 
-// Fills the padded layout from a compact (V|m|h|n) device buffer.
+// Fills the padded layout from a compact (u|m|h|n) device buffer (bit-exact).
 fib_status scatter_state(fib_ctx* c, const float* src) {
   fib_status st = check_launch(c, launch_fill_layout(c->d_fibers, c->n_fibers, st_u(c), st_m(c), st_h(c), st_n(c),
                                                      nullptr, (float)c->p.Vrest, (float)c->m0, (float)c->h0,
@@ -416,7 +417,7 @@ fib_status scatter_state(fib_ctx* c, const float* src) {
                                "fill");
   if (st != FIB_OK) return st;
   ++c->launches;
-  const float adds[4] = {(float)-c->p.Vrest, 0.f, 0.f, 0.f};
+  const float adds[4] = {0.f, 0.f, 0.f, 0.f};
   float* dst[4] = {st_u(c), st_m(c), st_h(c), st_n(c)};
   for (int k = 0; k < 4; ++k) {
     st = check_launch(c, launch_scatter(c->d_fibers, c->n_fibers, src + k * c->total, dst[k], adds[k], c->stream),
