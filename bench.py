@@ -42,9 +42,13 @@ WORKLOAD = "bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz"
 # Algorithmic work per node-update of the plain FP32 path:
 BYTES_PER_NODE_UPDATE = 32.0     # read + write V, m, h, n (FP32) once per split step
 FMA_OPS_PER_NODE_UPDATE = 238.0  # FP32 FMA-pipe operations of the method per split step
-MUFU_OPS_PER_NODE_UPDATE = 42.0  # 2^x and 1/x special-function operations per split step
-FP32_LANES_PER_SM = 128
-MUFU_LANES_PER_SM = 16
+EX2_OPS_PER_NODE_UPDATE = 24.0   # 2^x special-function operations per split step (4 per HH RHS)
+RCP_OPS_PER_NODE_UPDATE = 18.0   # 1/x special-function operations per split step (3 per HH RHS)
+# Per-SM per-clock unit rates on GB300 (FP32 FMA lanes; XU pipe rates of
+# ex2.approx and rcp.approx, which share the special-function pipe).
+FP32_LANES_PER_SM = 128.0
+EX2_PER_SM = 32.0
+RCP_PER_SM = 16.0
 
 
 def _env_int(k, d):
@@ -202,7 +206,8 @@ def run_gpu(args, world, rank, local, dist):
     total = w.total_nodes
     stream = torch.cuda.Stream(device=dev)
     tuning = dict(nodes_per_thread=args.nodes_per_thread, warps_per_cta=args.warps_per_cta,
-                  steps_per_launch=args.steps_per_launch, graph_steps=args.graph_steps)
+                  steps_per_launch=args.steps_per_launch, graph_steps=args.graph_steps,
+                  reaction_pairs=args.reaction_pairs)
 
     def barrier():
         if dist is not None:
@@ -272,10 +277,12 @@ def run_gpu(args, world, rank, local, dist):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     per_gpu_rate = float(total) * args.steps / (ms / 1e3)
-    # ALU roofline: node-updates/s if the binding FP32 or MUFU pipe ran at its
-    # full rate on every SM at the maximum SM clock.
-    alu_peak = n_sm * sm_max * min(FP32_LANES_PER_SM / FMA_OPS_PER_NODE_UPDATE,
-                                   MUFU_LANES_PER_SM / MUFU_OPS_PER_NODE_UPDATE)
+    # ALU roofline: node-updates/s if the binding pipe (FP32 FMA or the
+    # special-function XU pipe) ran at its full rate on every SM at the
+    # maximum SM clock.
+    fma_clk = FMA_OPS_PER_NODE_UPDATE / FP32_LANES_PER_SM
+    xu_clk = EX2_OPS_PER_NODE_UPDATE / EX2_PER_SM + RCP_OPS_PER_NODE_UPDATE / RCP_PER_SM
+    alu_peak = n_sm * sm_max / max(fma_clk, xu_clk)
     kernel_ms = ms / max(split_launches, 1)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "split_step_traffic.json")
@@ -307,9 +314,9 @@ def run_gpu(args, world, rank, local, dist):
             "frac": per_gpu_rate / alu_peak, "traffic": traffic,
             "kernel": "split_step_kernel", "kernel_ms_per_launch": kernel_ms,
             "algorithmic_bytes_per_launch": BYTES_PER_NODE_UPDATE * total * S,
-            "peak_derivation": f"{n_sm} SMs x {sm_max / 1e6:.0f} MHz x min(128 FP32 lanes / "
-                               f"{FMA_OPS_PER_NODE_UPDATE:.0f} FMA ops, 16 MUFU lanes / "
-                               f"{MUFU_OPS_PER_NODE_UPDATE:.0f} MUFU ops) per node-update",
+            "peak_derivation": f"{n_sm} SMs x {sm_max / 1e6:.0f} MHz / max(FMA {FMA_OPS_PER_NODE_UPDATE:.0f} ops "
+                               f"/ 128 lanes = {fma_clk:.3f} clk, XU {EX2_OPS_PER_NODE_UPDATE:.0f} ex2 / 32 + "
+                               f"{RCP_OPS_PER_NODE_UPDATE:.0f} rcp / 16 = {xu_clk:.3f} clk) per node-update",
             "hbm_equivalent": {"achieved_gbs": per_gpu_rate * BYTES_PER_NODE_UPDATE / 1e9, "peak_gbs": hbm_peak,
                                "frac": per_gpu_rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak,
                                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
@@ -336,6 +343,7 @@ def main():
     ap.add_argument("--warps-per-cta", type=int, default=0)
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--graph-steps", type=int, default=1000)
+    ap.add_argument("--reaction-pairs", type=int, default=0, help="1 scalar, 2 packed FP32x2, 0 auto")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-fibers", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=400)

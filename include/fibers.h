@@ -90,6 +90,8 @@ typedef struct {
   int32_t warps_per_cta;     /* CTA size in warps (1..32); fibers are packed by whole warps */
   int32_t steps_per_launch;  /* split steps each kernel launch keeps on chip */
   int32_t graph_steps;       /* split steps per captured CUDA graph (0 = no graphs) */
+  int32_t reaction_pairs;    /* 1: one node per FP32 instruction; 2: node pairs with packed
+                                FP32x2 instructions (same results bit for bit); 0: automatic */
 } fib_tuning;
 
 /* Creates a context for n_fibers fibers and copies the inputs to the device.

@@ -191,6 +191,7 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   if (W < 1 || W > kMaxWarpsPerCta) return fail(c, FIB_EINVAL, "warps_per_cta must be in [1, %d]", kMaxWarpsPerCta);
   if (W < w_max) return fail(c, FIB_EINVAL, "warps_per_cta %d < %d warps needed by the longest fiber", W, w_max);
   if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
+  if (t.reaction_pairs < 0 || t.reaction_pairs > 2) return fail(c, FIB_EINVAL, "reaction_pairs must be 0, 1 or 2");
 
   // length classes
   std::map<int32_t, int> cls;
@@ -264,6 +265,7 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   c->tune.warps_per_cta = W;
   c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
   c->tune.graph_steps = t.graph_steps;
+  c->tune.reaction_pairs = t.reaction_pairs ? t.reaction_pairs : 1;
 
   const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
   const size_t es = fp64 ? 8 : 4;
@@ -336,6 +338,7 @@ StepArgs make_args(fib_ctx* c) {
   a.n_levels = c->levels;
   a.rec_stride = c->rec_stride;
   a.W = c->W;
+  a.packed = c->tune.reaction_pairs == 2 ? 1 : 0;
   return a;
 }
 
@@ -487,8 +490,7 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
   cudaError_t e = cudaGetDevice(&cx->device);
   if (e != cudaSuccess) return fail(nullptr, FIB_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   cx->stream = static_cast<cudaStream_t>(cuda_stream);
-  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000};
-  if (!tuning) t.graph_steps = 1000;
+  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000, 0};
   st = build_layout(cx, t);
   if (st == FIB_OK) {
     if ((e = cudaStreamCreateWithFlags(&cx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -750,8 +752,9 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
     if (w_max > kMaxWarpsPerCta) continue;
     std::vector<int> Ws{auto_W(w_max)};
     if (w_max * 2 <= kMaxWarpsPerCta && auto_W(w_max) != w_max) Ws.push_back(w_max);
-    for (int W : Ws) {
-      fib_tuning t{K, W, start.steps_per_launch, start.graph_steps};
+    for (int W : Ws)
+     for (int pairs : {1, 2}) {
+      fib_tuning t{K, W, start.steps_per_launch, start.graph_steps, pairs};
       if (build_layout(c, t) != FIB_OK) continue;
       if (need > 0 && scatter_state(c, keep) != FIB_OK) continue;
       StepArgs a = make_args(c);

@@ -71,7 +71,7 @@ struct StepArgs {
   int32_t n_levels;        // cyclic-reduction levels kept
   int32_t rec_stride;      // elements per thread record
   int32_t W;               // warps per CTA
-  int32_t pad;
+  int32_t packed;          // 1: reaction step on node pairs with FP32x2 arithmetic
 };
 
 // Host-built solver tables for one (K, r, fiber-length set).

@@ -205,6 +205,14 @@ def test_graph_eager_and_launch_blocking_are_bitwise_identical():
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+def test_packed_fp32x2_reaction_is_bitwise_identical_to_scalar():
+    w = _edge_workload(700, seed=13)
+    for K in (8, 12, 16):
+        a = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=1))
+        b = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=2))
+        assert np.array_equal(a, b), K
+
+
 def test_checkpoint_resume_is_bitwise():
     w = _edge_workload(900, seed=6)
     full = gpu_checkpoints(w, [900])[0]
