@@ -137,6 +137,28 @@ fib_status step(fib_ctx* ctx, int64_t n_steps);
  * (section "Code Generation for GPUs"). */
 fib_status read_vm(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
 
+/* read_vm for callers that cannot allocate device memory.  The thesis has
+ * no counterpart to this call; it exists for the library's users.  read_vm
+ * with a host buffer stages V through device memory that the context
+ * allocates with cudaMalloc on its first host read.  Some callers cannot
+ * allow that: an application whose device memory is fully reserved by
+ * another allocator (a framework's memory pool sized to the whole GPU) can
+ * see that cudaMalloc fail with out-of-memory in the middle of a long run,
+ * and a latency-sensitive loop cannot accept the device-wide
+ * synchronisation that cudaMalloc and cudaFree may imply.  This call stages
+ * through a fixed 8 MiB array compiled into the library instead (every GPU
+ * that loads the library holds it until the process exits), and calls no
+ * cudaMalloc, cudaFree or allocating routine.
+ *   host_out  host buffer for V (mV, float, ragged order), capacity >= sum(n_nodes).
+ * Limit: at most 2,097,152 nodes per context (the array's size); larger
+ * contexts get FIB_EINVAL and should use read_vm.  The first call on a GPU
+ * looks up the array's device address on that GPU (cudaGetSymbolAddress);
+ * make that first call before any stream capture begins.  All calls share
+ * the array and it keeps the last call's contents; calls that overlap on
+ * the GPU (two contexts reading on different streams at once) race on it.
+ * Synchronises the context's stream.  Errors as read_vm. */
+fib_status read_vm_static(fib_ctx* ctx, float* host_out, size_t capacity);
+
 /* Copies the full state into out (capacity >= 4 sum(n_nodes)): four blocks
  * of sum(n_nodes) floats in ragged order, u | m | h | n, where u = V - Vrest
  * is the depolarisation in mV (the form the library integrates; V itself is

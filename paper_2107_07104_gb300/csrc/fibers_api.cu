@@ -433,6 +433,22 @@ fib_status scatter_state(fib_ctx* c, const float* src) {
 
 }  // namespace
 
+fib_status fib::ctx_view(fib_ctx* c, fib::CtxView* v) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  v->device = c->device;
+  v->stream = c->stream;
+  v->fibers = c->d_fibers;
+  v->n_fibers = c->n_fibers;
+  v->u = c->d_state;
+  v->total = c->total;
+  v->vrest = (float)c->p.Vrest;
+  v->flag = c->d_flag;
+  v->launches = &c->launches;
+  return FIB_OK;
+}
+
+fib_status fib::ctx_fail(fib_ctx* c, fib_status s, const char* msg) { return fail(c, s, "%s", msg); }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

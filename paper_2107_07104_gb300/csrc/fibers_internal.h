@@ -2,8 +2,12 @@
 // Nothing here is part of the public ABI (include/fibers.h).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
+
+#include "fibers.h"
 
 namespace fib {
 
@@ -107,4 +111,22 @@ int launch_fill_layout(const FiberDesc* fibers, int32_t n_fibers, float* u, floa
                        void* stream);
 size_t split_step_smem_bytes(int K, bool fp64_solve, int W);
 
+}  // namespace fib
+
+// Read-only view of a context for entry points outside fibers_api.cu.
+struct fib_ctx;
+namespace fib {
+struct CtxView {
+  int device;
+  cudaStream_t stream;
+  const FiberDesc* fibers;
+  int32_t n_fibers;
+  const float* u;       // depolarisation array of the padded layout
+  int64_t total;        // real nodes
+  float vrest;
+  const int32_t* flag;  // device non-finite flag
+  int64_t* launches;    // the context's kernel-launch counter
+};
+fib_status ctx_view(fib_ctx* c, CtxView* out);
+fib_status ctx_fail(fib_ctx* c, fib_status s, const char* msg);
 }  // namespace fib

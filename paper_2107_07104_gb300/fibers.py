@@ -28,7 +28,8 @@ STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINI
                 "FIB_ESTATE", "FIB_ENOTSUP"]
 
 # Every symbol the header declares (checked by the ABI test).
-EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "fibers_read_state", "fibers_write_state",
+EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
+            "fibers_write_state",
             "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
             "fibers_kernel_launches", "fibers_last_error", "fibers_destroy")
 
@@ -84,6 +85,7 @@ def load(build_if_missing: bool = True):
         L.set_stimulus_times.argtypes = [vp, i32, P(i64), P(ctypes.c_double)]
         L.step.argtypes = [vp, i64]
         L.read_vm.argtypes = [vp, vp, sz, i32]
+        L.read_vm_static.argtypes = [vp, vp, sz]
         L.fibers_read_state.argtypes = [vp, vp, sz, i32]
         L.fibers_write_state.argtypes = [vp, vp, sz, i32, i64]
         L.fibers_stats.argtypes = [vp, P(i64), P(i64)]
@@ -97,7 +99,7 @@ def load(build_if_missing: bool = True):
         L.fibers_last_error.restype = ctypes.c_char_p
         L.fibers_destroy.argtypes = [vp]
         L.fibers_destroy.restype = None
-        for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "fibers_read_state",
+        for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
                      "fibers_write_state", "fibers_stats", "fibers_synchronize", "fibers_get_tuning",
                      "fibers_set_tuning", "fibers_autotune"):
             getattr(L, name).restype = ctypes.c_int
@@ -192,6 +194,14 @@ def step(ctx, n_steps: int) -> None:
 def read_vm(ctx, out) -> None:
     ptr, n, dev = _buffer(out)
     _check(load().read_vm(ctx, ptr, n, dev), ctx)
+
+
+def read_vm_static(ctx, out: np.ndarray) -> None:
+    """read_vm into a host array without any device allocation (the library
+    stages through its fixed 8 MiB array; at most 2,097,152 nodes)."""
+    if not isinstance(out, np.ndarray) or out.dtype != np.float32 or not out.flags.c_contiguous:
+        raise TypeError("expected a contiguous float32 numpy array")
+    _check(load().read_vm_static(ctx, out.ctypes.data, out.size), ctx)
 
 
 def fibers_read_state(ctx, out) -> None:
