@@ -207,7 +207,7 @@ def run_gpu(args, world, rank, local, dist):
     stream = torch.cuda.Stream(device=dev)
     tuning = dict(nodes_per_thread=args.nodes_per_thread, warps_per_cta=args.warps_per_cta,
                   steps_per_launch=args.steps_per_launch, graph_steps=args.graph_steps,
-                  reaction_pairs=args.reaction_pairs)
+                  reaction_pairs=args.reaction_pairs, ctas_per_sm=args.ctas_per_sm)
 
     def barrier():
         if dist is not None:
@@ -344,6 +344,7 @@ def main():
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--graph-steps", type=int, default=1000)
     ap.add_argument("--reaction-pairs", type=int, default=0, help="1 scalar, 2 packed FP32x2, 0 auto")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="register budget: 2 or 3 CTAs per SM, 0 auto")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-fibers", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=400)

@@ -92,6 +92,8 @@ typedef struct {
   int32_t graph_steps;       /* split steps per captured CUDA graph (0 = no graphs) */
   int32_t reaction_pairs;    /* 1: one node per FP32 instruction; 2: node pairs with packed
                                 FP32x2 instructions (same results bit for bit); 0: automatic */
+  int32_t ctas_per_sm;       /* register budget of the step kernel: 2 (up to 128 registers per
+                                thread) or 3 (up to 85, more warps per SM); 0: automatic */
 } fib_tuning;
 
 /* Creates a context for n_fibers fibers and copies the inputs to the device.

@@ -146,10 +146,14 @@ int warps_for(int32_t n, int K) {
 }
 
 int auto_K(const std::vector<int32_t>& n_nodes) {
-  // fewest padded nodes (lanes x K) over the whole bundle; ties go to 12
+  // K = 8 (measured fastest on GB300 with packed pairs and the 85-register
+  // budget) whenever every fiber fits; otherwise the fewest padded nodes
+  int max_n = 0;
+  for (int32_t n : n_nodes) max_n = std::max(max_n, n);
+  if (warps_for(max_n, 8) <= kMaxWarpsPerCta) return 8;
   int best = 12;
   int64_t best_pad = -1;
-  for (int K : {12, 16, 8}) {
+  for (int K : {12, 16}) {
     int64_t pad = 0;
     bool ok = true;
     for (int32_t n : n_nodes) {
@@ -192,6 +196,8 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   if (W < w_max) return fail(c, FIB_EINVAL, "warps_per_cta %d < %d warps needed by the longest fiber", W, w_max);
   if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
   if (t.reaction_pairs < 0 || t.reaction_pairs > 2) return fail(c, FIB_EINVAL, "reaction_pairs must be 0, 1 or 2");
+  if (t.ctas_per_sm != 0 && t.ctas_per_sm != 2 && t.ctas_per_sm != 3)
+    return fail(c, FIB_EINVAL, "ctas_per_sm must be 0, 2 or 3");
 
   // length classes
   std::map<int32_t, int> cls;
@@ -265,7 +271,8 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   c->tune.warps_per_cta = W;
   c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
   c->tune.graph_steps = t.graph_steps;
-  c->tune.reaction_pairs = t.reaction_pairs ? t.reaction_pairs : 1;
+  c->tune.reaction_pairs = t.reaction_pairs ? t.reaction_pairs : 2;
+  c->tune.ctas_per_sm = t.ctas_per_sm ? t.ctas_per_sm : (K == 8 ? 3 : 2);
 
   const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
   const size_t es = fp64 ? 8 : 4;
@@ -329,6 +336,9 @@ StepArgs make_args(fib_ctx* c) {
   a.hh.uL = (float)(c->EL - c->p.Vrest);
   a.hh.stim = (float)(c->p.stim_amplitude / Cm);
   a.hh.dt0 = (float)c->p.dt_0d;
+  a.hh.gNa_uNa = (float)((c->p.gNa / Cm) * (c->p.ENa - c->p.Vrest));
+  a.hh.gK_uK = (float)((c->p.gK / Cm) * (c->p.EK - c->p.Vrest));
+  a.hh.gL_uL = (float)((c->p.gL / Cm) * (c->EL - c->p.Vrest));
   a.r = c->r;
   a.n_sub = (int32_t)c->n_sub;
   a.n_cn = (int32_t)c->n_cn;
@@ -339,6 +349,7 @@ StepArgs make_args(fib_ctx* c) {
   a.rec_stride = c->rec_stride;
   a.W = c->W;
   a.packed = c->tune.reaction_pairs == 2 ? 1 : 0;
+  a.lean = c->tune.ctas_per_sm == 3 ? 1 : 0;
   return a;
 }
 
@@ -506,7 +517,7 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
   cudaError_t e = cudaGetDevice(&cx->device);
   if (e != cudaSuccess) return fail(nullptr, FIB_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   cx->stream = static_cast<cudaStream_t>(cuda_stream);
-  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000, 0};
+  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000, 0, 0};
   st = build_layout(cx, t);
   if (st == FIB_OK) {
     if ((e = cudaStreamCreateWithFlags(&cx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -769,8 +780,9 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
     std::vector<int> Ws{auto_W(w_max)};
     if (w_max * 2 <= kMaxWarpsPerCta && auto_W(w_max) != w_max) Ws.push_back(w_max);
     for (int W : Ws)
-     for (int pairs : {1, 2}) {
-      fib_tuning t{K, W, start.steps_per_launch, start.graph_steps, pairs};
+     for (int pairs : {1, 2})
+      for (int occ : {2, 3}) {
+      fib_tuning t{K, W, start.steps_per_launch, start.graph_steps, pairs, occ};
       if (build_layout(c, t) != FIB_OK) continue;
       if (need > 0 && scatter_state(c, keep) != FIB_OK) continue;
       StepArgs a = make_args(c);

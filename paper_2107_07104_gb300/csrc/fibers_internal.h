@@ -48,6 +48,7 @@ struct HHConst {  // Hodgkin-Huxley constants in the depolarisation u = V - Vres
   float uNa, uK, uL;  // reversal potentials - Vrest
   float stim;         // stimulus amplitude / Cm
   float dt0;          // Heun substep width
+  float gNa_uNa, gK_uK, gL_uL;  // products of the above, rounded once from FP64
 };
 
 struct StepArgs {
@@ -76,6 +77,8 @@ struct StepArgs {
   int32_t rec_stride;      // elements per thread record
   int32_t W;               // warps per CTA
   int32_t packed;          // 1: reaction step on node pairs with FP32x2 arithmetic
+  int32_t lean;            // 1: kernel built for 3 CTAs of 256 threads per SM (<= 85 registers)
+  int32_t pad2;
 };
 
 // Host-built solver tables for one (K, r, fiber-length set).

@@ -205,12 +205,15 @@ def test_graph_eager_and_launch_blocking_are_bitwise_identical():
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
-def test_packed_fp32x2_reaction_is_bitwise_identical_to_scalar():
+def test_reaction_forms_and_register_budgets_are_bitwise_identical():
+    """Packed FP32x2 pairs and the 85-register build compute the same bits as
+    the scalar 128-register build."""
     w = _edge_workload(700, seed=13)
     for K in (8, 12, 16):
-        a = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=1))
-        b = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=2))
-        assert np.array_equal(a, b), K
+        a = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=1, ctas_per_sm=2))
+        for pairs, occ in ((2, 2), (1, 3), (2, 3)):
+            b = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=pairs, ctas_per_sm=occ))
+            assert np.array_equal(a, b), (K, pairs, occ)
 
 
 def test_checkpoint_resume_is_bitwise():
