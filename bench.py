@@ -347,7 +347,7 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="register budget: 2 or 3 CTAs per SM, 0 auto")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-fibers", type=int, default=256)
-    ap.add_argument("--cpu-steps", type=int, default=400)
+    ap.add_argument("--cpu-steps", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
