@@ -125,6 +125,40 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("split_step.cu", "fibers_internal.h"):
+        with open(os.path.join(ROOT, "paper_2107_07104_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic_from_profile(tune):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the kernel source or the launch shape changed since."""
+    path = os.path.join(ROOT, "profiles", "split_step_kernel_bundle7744_ncu.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        same = (fields.get("kernel source sha256[:16]") == kernel_source_hash()
+                and int(fields.get("steps_per_launch", -1)) == tune["steps_per_launch"]
+                and int(fields.get("nodes_per_thread", -1)) == tune["nodes_per_thread"]
+                and int(fields.get("reaction_pairs", -1)) == tune["reaction_pairs"]
+                and int(fields.get("ctas_per_sm", -1)) == tune["ctas_per_sm"])
+        return float(fields["dram bytes per launch"]) if same else None
+    except (KeyError, ValueError):
+        return None
+
+
 def dist_setup():
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -284,16 +318,7 @@ def run_gpu(args, world, rank, local, dist):
     xu_clk = EX2_OPS_PER_NODE_UPDATE / EX2_PER_SM + RCP_OPS_PER_NODE_UPDATE / RCP_PER_SM
     alu_peak = n_sm * sm_max / max(fma_clk, xu_clk)
     kernel_ms = ms / max(split_launches, 1)
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "split_step_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                pj = json.load(f)
-            if pj.get("steps_per_launch") == S and pj.get("nodes_per_thread") == tune["nodes_per_thread"]:
-                traffic = pj.get("dram_bytes_per_launch_full_bundle")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = dram_traffic_from_profile(tune)
     cpu = None
     if not args.no_cpu_baseline:
         rate, dt, cores, nodes = oracle_rate(w, args.cpu_fibers, args.cpu_steps)
