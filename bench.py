@@ -326,6 +326,7 @@ def run_gpu(args, world, rank, local, dist):
                "sample": f"first {args.cpu_fibers} of 7744 fibers x 1481 nodes, {args.cpu_steps} split steps "
                          f"({dt:.1f} s of FP64 oracle on {cores} threads)"}
     clocks = clk.summary()
+    sur = None if args.no_surrogate else surrogate_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
@@ -353,9 +354,72 @@ def run_gpu(args, world, rank, local, dist):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "finite": finite,
+        "surrogate": sur,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def activation_times(samples, dt):
+    """First upward 0 mV crossing per node (linear interpolation), NaN if none."""
+    s = np.asarray(samples, np.float64)
+    cross = (s[:-1] < 0) & (s[1:] >= 0)
+    t = np.full(s.shape[1], np.nan)
+    idx = np.nonzero(cross.any(axis=0))[0]
+    k = np.argmax(cross, axis=0)[idx]
+    v0, v1 = s[k, idx], s[k + 1, idx]
+    t[idx] = (k + 1 + (0.0 - v0) / (v1 - v0)) * dt
+    return t
+
+
+def surrogate_leg(args, w, tune, stream, dev, total, plain_rate):
+    """Node-updates/s of the surrogate path on the same bundle, and its
+    agreement with the plain FP32 path on 64 firing fibers over 20 ms."""
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+    from paper_2107_07104_gb300 import surrogate as S
+    blob = S.load_blob()
+    fib = F.Fibers.from_workload(w, tuning=tune, stream=stream, mode=F.FIB_MODE_SURROGATE)
+    F.fibers_load_surrogate(fib.ctx, blob)
+    fib.step(args.warmup)
+    fib.synchronize()
+    _, fb0 = fib.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    fib.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, fb1 = fib.stats()
+    fib.close()
+    rate = float(total) * args.steps / (ms / 1e3)
+    firing = [f for f in range(w.n_fibers) if w.mu_offsets[w.mu_of_fiber[f] + 1] > w.mu_offsets[w.mu_of_fiber[f]]]
+    sub = w.subset(np.sort(np.random.default_rng(9).choice(firing, min(64, len(firing)), replace=False)))
+    every = 10
+    traj = {}
+    for mode in (F.FIB_MODE_FP32, F.FIB_MODE_SURROGATE):
+        with F.Fibers.from_workload(sub, mode=mode) as f:
+            if mode == F.FIB_MODE_SURROGATE:
+                F.fibers_load_surrogate(f.ctx, blob)
+            rows = []
+            for _ in range(sub.n_steps // every):
+                f.step(every)
+                rows.append(f.read_vm().astype(np.float64))
+            traj[mode] = np.array(rows)
+    a, b = traj[F.FIB_MODE_FP32], traj[F.FIB_MODE_SURROGATE]
+    ta, tb = activation_times(a, every * sub.params["dt_split"]), activation_times(b, every * sub.params["dt_split"])
+    both = ~np.isnan(ta) & ~np.isnan(tb)
+    return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
+            "network_fraction_of_node_updates": 1.0 - (fb1 - fb0) / (float(total) * args.steps),
+            "accuracy_vs_plain_fp32": {
+                "fibers": int(sub.n_fibers), "simulated_ms": sub.n_steps * sub.params["dt_split"],
+                "activation_time_max_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
+                "activated_nodes": int((~np.isnan(ta)).sum()), "matched_nodes": int(both.sum()),
+                "rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(a)),
+                "max_abs_mv": float(np.max(np.abs(a - b)))},
+            "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}
 
 
 def main():
@@ -374,6 +438,7 @@ def main():
     ap.add_argument("--cpu-fibers", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -193,6 +193,74 @@ fib_status fibers_set_tuning(fib_ctx* ctx, const fib_tuning* tuning);
  * Synchronises. */
 fib_status fibers_autotune(fib_ctx* ctx, int32_t n_trial_steps, fib_tuning* best);
 
+/* ---------------------------------------------------------------------------
+ * Reaction-step surrogate (FIB_MODE_SURROGATE).
+ *
+ * A small network replaces the reaction part of each split step (the Heun
+ * substeps of the HH model, eq:heun, sec:subcelullar_model); the diffusion
+ * halves stay exact.  The thesis has no learned component on this path.
+ * Network: x = normalised (u, m, h, n, s) -> 128 -> SiLU -> 128 -> SiLU -> 4
+ * outputs, the normalised change of (u, m, h, n) over one split step, where
+ * u = V - Vrest and s is the fraction of the step's Heun substeps with the
+ * stimulus on.  SiLU(z) = z / (1 + exp(-z)).  Inference runs on BF16 tensor
+ * cores with FP32 accumulation; every input is split into bf16 high and low
+ * parts so the first layer sees it to FP32 accuracy.  A node whose input lies
+ * outside the training envelope is advanced by the plain HH step instead.
+ *
+ * Parameter vector theta (FP32, kNumParams = 17796 values): W1 (128 x 5,
+ * row-major), b1 (128), W2 (128 x 128), b2 (128), W3 (4 x 128), b3 (4).
+ * ------------------------------------------------------------------------- */
+
+/* Loads a trained surrogate into a context created with FIB_MODE_SURROGATE.
+ *   blob      host array of n_floats = 17837 floats: 5, 128, 4, then
+ *             in_mu[5], in_sigma[5] (x = (raw - in_mu) / in_sigma),
+ *             out_mu[4], out_sigma[4] (change = out * out_sigma + out_mu),
+ *             env_lo[5], env_hi[5] (raw inputs outside [lo, hi] use the
+ *             plain HH step), quiet_lo[5], quiet_hi[5] (raw inputs inside
+ *             this box around rest also use the plain HH step, which keeps
+ *             rest an exact fixed point), theta[17796].
+ * raw = (u, m, h, n, s). 
+ * Copied; the caller keeps the blob.  Errors: FIB_EINVAL (size, shape,
+ * non-finite values, in_sigma <= 0), FIB_ESTATE (not a surrogate context). */
+fib_status fibers_load_surrogate(fib_ctx* ctx, const float* blob, size_t n_floats);
+
+/* The plain reaction step (dt_split / dt_0d Heun substeps of the HH model,
+ * eq:heun) on `count` independent nodes, for generating training targets.
+ *   in        device, 4 x count floats: V (mV) | m | h | n.
+ *   stim_mask device, count bytes (bit k: stimulus on during substep k), or NULL.
+ *   out       device, 4 x count floats, same layout as in.
+ * Asynchronous on cuda_stream.  Errors: FIB_EINVAL, FIB_ECUDA. */
+fib_status fibers_hh_reaction(const fib_params* p, int64_t count, const float* in, const uint8_t* stim_mask,
+                              float* out, void* cuda_stream);
+
+/* One training step of the surrogate network on a batch (device buffers):
+ * forward pass, mean-squared-error loss over the batch and the 4 outputs, and
+ * the gradient of the loss with respect to theta.  With quantize != 0 the
+ * forward pass rounds weights and matrix-product inputs to bfloat16 (round to
+ * nearest even) as inference does, and the gradient treats that rounding as
+ * the identity.
+ *   theta     17796 floats.      x       batch x 5 normalised inputs.
+ *   target    batch x 4.         workspace >= batch x 784 floats (scratch).
+ *   grad      17796 floats (out). loss   1 float (out, device).
+ * Asynchronous.  Errors: FIB_EINVAL, FIB_ECUDA. */
+fib_status fibers_mlp_train_step(const float* theta, int32_t quantize, const float* x, const float* target,
+                                 int64_t batch, float* workspace, float* grad, float* loss, void* cuda_stream);
+
+/* Forward pass only: out (batch x 4) for inputs x (batch x 5); workspace >=
+ * batch x 512 floats.  Asynchronous. */
+fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float* x, int64_t batch, float* workspace,
+                              float* out, void* cuda_stream);
+
+/* One Adam update of n parameters in place (Kingma & Ba 2015, with bias
+ * correction for step t >= 1).  All buffers on the device.  Asynchronous. */
+fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad, int64_t n, float lr, float beta1,
+                            float beta2, float eps, int64_t t, void* cuda_stream);
+
+/* Per-column mean, standard deviation, minimum and maximum of a device matrix
+ * X (n x cols, row-major) into out (host, 4 x cols doubles, column by column:
+ * mean, std, min, max).  Synchronises cuda_stream.  cols <= 64. */
+fib_status fibers_feature_stats(const float* X, int64_t n, int32_t cols, double* out, void* cuda_stream);
+
 /* Number of launches of this library's kernels enqueued so far by ctx. */
 int64_t fibers_kernel_launches(const fib_ctx* ctx);
 

@@ -18,6 +18,9 @@
 
 #include "fibers.h"
 #include "fibers_internal.h"
+#include "surrogate_internal.h"
+
+#include <cuda_bf16.h>
 
 using namespace fib;
 
@@ -63,6 +66,17 @@ struct fib_ctx {
 
   cudaGraphExec_t graph = nullptr;
   int64_t graph_launches = 0;
+
+  // reaction-step surrogate (FIB_MODE_SURROGATE)
+  int32_t* d_slot_fiber = nullptr;   // fiber of every slot
+  uint8_t* d_fiber_stim = nullptr;   // per-fiber stimulus substep mask of the current step
+  uint16_t* d_sur_wts = nullptr;     // bf16 weight images
+  float* d_sur_bias = nullptr;
+  unsigned long long* d_fallback = nullptr;
+  bool sur_loaded = false;
+  float in_mu[kIn] = {}, in_inv_sigma[kIn] = {}, out_mu[kOut] = {}, out_sigma[kOut] = {};
+  float env_lo[kIn] = {}, env_hi[kIn] = {};
+  float quiet_lo[kIn] = {}, quiet_hi[kIn] = {};
 
   std::string err;
 };
@@ -128,7 +142,6 @@ fib_status validate(const fib_params* p) {
     return fail(nullptr, FIB_EINVAL, "stim_half_width must be in [0, 8]");
   if (p->mode != FIB_MODE_FP32 && p->mode != FIB_MODE_FP64_THOMAS && p->mode != FIB_MODE_SURROGATE)
     return fail(nullptr, FIB_EINVAL, "unknown mode %d", p->mode);
-  if (p->mode == FIB_MODE_SURROGATE) return fail(nullptr, FIB_ENOTSUP, "surrogate mode is not available in this build");
   if (p->flags != 0 || p->reserved != 0) return fail(nullptr, FIB_EINVAL, "flags and reserved must be 0");
   const double q0 = p->dt_split / p->dt_0d, q1 = 0.5 * p->dt_split / p->dt_1d;
   const double r0 = std::nearbyint(q0), r1 = std::nearbyint(q1);
@@ -179,6 +192,7 @@ void free_layout(fib_ctx* c) {
   dfree(c->d_warps);
   dfree(c->d_rows);
   dfree(c->d_recs);
+  dfree(c->d_slot_fiber);
 }
 
 // Builds the padded layout, CTA packing and solver tables for tuning t.
@@ -282,6 +296,13 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   CU(c, cudaMalloc(&c->d_rows, es * tab.rows.size()));
   CU(c, cudaMalloc(&c->d_recs, es * std::max<size_t>(tab.recs.size(), 1)));
   if (!fd.empty()) CU(c, cudaMemcpy(c->d_fibers, fd.data(), sizeof(FiberDesc) * fd.size(), cudaMemcpyHostToDevice));
+  if (c->p.mode == FIB_MODE_SURROGATE && slot > 0) {
+    std::vector<int32_t> sf((size_t)slot, -1);
+    for (int32_t f = 0; f < c->n_fibers; ++f)
+      for (int32_t i = 0; i < fd[f].slot_len; ++i) sf[(size_t)fd[f].slot + i] = f;
+    CU(c, cudaMalloc(&c->d_slot_fiber, sizeof(int32_t) * sf.size()));
+    CU(c, cudaMemcpy(c->d_slot_fiber, sf.data(), sizeof(int32_t) * sf.size(), cudaMemcpyHostToDevice));
+  }
   if (!wm.empty()) CU(c, cudaMemcpy(c->d_warps, wm.data(), sizeof(WarpMap) * wm.size(), cudaMemcpyHostToDevice));
   if (fp64) {
     CU(c, cudaMemcpy(c->d_rows, tab.rows.data(), 8 * tab.rows.size(), cudaMemcpyHostToDevice));
@@ -313,6 +334,31 @@ fib_status check_launch(fib_ctx* c, int e, const char* what) {
   return FIB_OK;
 }
 
+HHConst hh_const(const fib_params& p, double EL) {
+  HHConst h{};
+  const double Cm = p.Cm;
+  h.gNa = (float)(p.gNa / Cm);
+  h.gK = (float)(p.gK / Cm);
+  h.gL = (float)(p.gL / Cm);
+  h.uNa = (float)(p.ENa - p.Vrest);
+  h.uK = (float)(p.EK - p.Vrest);
+  h.uL = (float)(EL - p.Vrest);
+  h.stim = (float)(p.stim_amplitude / Cm);
+  h.dt0 = (float)p.dt_0d;
+  h.gNa_uNa = (float)((p.gNa / Cm) * (p.ENa - p.Vrest));
+  h.gK_uK = (float)((p.gK / Cm) * (p.EK - p.Vrest));
+  h.gL_uL = (float)((p.gL / Cm) * (EL - p.Vrest));
+  return h;
+}
+
+double exact_leak_reversal(const fib_params& p) {
+  double m0, h0, n0;
+  rest_gates(0.0, &m0, &h0, &n0);
+  const double ina = p.gNa * m0 * m0 * m0 * h0 * (p.Vrest - p.ENa);
+  const double ik = p.gK * n0 * n0 * n0 * n0 * (p.Vrest - p.EK);
+  return p.Vrest + (ina + ik) / p.gL;
+}
+
 StepArgs make_args(fib_ctx* c) {
   StepArgs a{};
   a.u = st_u(c);
@@ -327,18 +373,7 @@ StepArgs make_args(fib_ctx* c) {
   a.fire_k = c->d_fire_k;
   a.step_base = c->d_step;
   a.flag = c->d_flag;
-  const double Cm = c->p.Cm;
-  a.hh.gNa = (float)(c->p.gNa / Cm);
-  a.hh.gK = (float)(c->p.gK / Cm);
-  a.hh.gL = (float)(c->p.gL / Cm);
-  a.hh.uNa = (float)(c->p.ENa - c->p.Vrest);
-  a.hh.uK = (float)(c->p.EK - c->p.Vrest);
-  a.hh.uL = (float)(c->EL - c->p.Vrest);
-  a.hh.stim = (float)(c->p.stim_amplitude / Cm);
-  a.hh.dt0 = (float)c->p.dt_0d;
-  a.hh.gNa_uNa = (float)((c->p.gNa / Cm) * (c->p.ENa - c->p.Vrest));
-  a.hh.gK_uK = (float)((c->p.gK / Cm) * (c->p.EK - c->p.Vrest));
-  a.hh.gL_uL = (float)((c->p.gL / Cm) * (c->EL - c->p.Vrest));
+  a.hh = hh_const(c->p, c->EL);
   a.r = c->r;
   a.n_sub = (int32_t)c->n_sub;
   a.n_cn = (int32_t)c->n_cn;
@@ -350,6 +385,7 @@ StepArgs make_args(fib_ctx* c) {
   a.W = c->W;
   a.packed = c->tune.reaction_pairs == 2 ? 1 : 0;
   a.lean = c->tune.ctas_per_sm == 3 ? 1 : 0;
+  a.phases = 7;
   return a;
 }
 
@@ -443,6 +479,60 @@ fib_status scatter_state(fib_ctx* c, const float* src) {
 }
 
 }  // namespace
+
+// Surrogate mode: diffusion halves by the step kernel (reaction phase off),
+// the reaction step by the tensor-core surrogate with per-node HH fallback.
+fib_status surrogate_steps(fib_ctx* c, int64_t n) {
+  if (c->n_ctas == 0) return FIB_OK;
+  StepArgs a = make_args(c);
+  a.n_steps = 1;
+  a.step_offset = 0;
+  const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
+  SurArgs s{};
+  s.u = st_u(c);
+  s.m = st_m(c);
+  s.h = st_h(c);
+  s.n = st_n(c);
+  s.fibers = c->d_fibers;
+  s.slot_fiber = c->d_slot_fiber;
+  s.fiber_stim = c->d_fiber_stim;
+  s.wts = c->d_sur_wts;
+  s.bias = c->d_sur_bias;
+  s.fallback_count = c->d_fallback;
+  s.n_slots = c->slots_total;
+  s.hh = a.hh;
+  for (int k = 0; k < kIn; ++k) {
+    s.in_mu[k] = c->in_mu[k];
+    s.in_inv_sigma[k] = c->in_inv_sigma[k];
+    s.env_lo[k] = c->env_lo[k];
+    s.env_hi[k] = c->env_hi[k];
+    s.quiet_lo[k] = c->quiet_lo[k];
+    s.quiet_hi[k] = c->quiet_hi[k];
+  }
+  for (int k = 0; k < kOut; ++k) {
+    s.out_mu[k] = c->out_mu[k];
+    s.out_sigma[k] = c->out_sigma[k];
+  }
+  s.n_sub = (int32_t)c->n_sub;
+  s.hw = c->p.stim_half_width;
+  a.phases = 1;
+  fib_status st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, c->stream), "diffusion");
+  if (st != FIB_OK) return st;
+  ++c->launches;
+  for (int64_t i = 0; i < n; ++i) {
+    st = check_launch(c, launch_fiber_stim(c->d_fibers, c->n_fibers, c->d_mu_off, c->d_fire_k, c->n_mu, c->d_step, i,
+                                           (int)c->n_sub, (int)c->pulse, c->d_fiber_stim, c->stream),
+                      "stimulus");
+    if (st != FIB_OK) return st;
+    st = check_launch(c, launch_sur_step(s, c->stream), "surrogate");
+    if (st != FIB_OK) return st;
+    a.phases = (i + 1 < n) ? (4 | 1) : 4;
+    st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, c->stream), "diffusion");
+    if (st != FIB_OK) return st;
+    c->launches += 3;
+  }
+  return FIB_OK;
+}
 
 fib_status fib::ctx_view(fib_ctx* c, fib::CtxView* v) {
   if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
@@ -599,6 +689,16 @@ fib_status step(fib_ctx* c, int64_t n_steps) {
   if (n_steps < 0) return fail(c, FIB_EINVAL, "n_steps < 0");
   if (n_steps == 0) return FIB_OK;
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  if (c->p.mode == FIB_MODE_SURROGATE) {
+    if (!c->sur_loaded) return fail(c, FIB_ESTATE, "surrogate mode needs fibers_load_surrogate before step");
+    fib_status st = surrogate_steps(c, n_steps);
+    if (st != FIB_OK) return st;
+    st = check_launch(c, launch_advance(c->d_step, n_steps, c->stream), "advance");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+    c->next_step += n_steps;
+    return FIB_OK;
+  }
   const int64_t G = c->tune.graph_steps;
   if (G > 0 && n_steps >= G && c->n_ctas > 0) {
     if (!c->graph) {
@@ -697,7 +797,11 @@ fib_status fibers_stats(fib_ctx* c, int64_t* steps_done, int64_t* fallback_nodes
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
   CU(c, cudaStreamSynchronize(c->stream));
   if (steps_done) *steps_done = c->next_step;
-  if (fallback_nodes) *fallback_nodes = 0;
+  if (fallback_nodes) {
+    unsigned long long fb = 0;
+    if (c->d_fallback) CU(c, cudaMemcpy(&fb, c->d_fallback, sizeof(fb), cudaMemcpyDeviceToHost));
+    *fallback_nodes = (int64_t)fb;
+  }
   return check_flag(c);
 }
 
@@ -829,6 +933,129 @@ const char* fibers_last_error(const fib_ctx* c) {
   return c->err.c_str();
 }
 
+fib_status fibers_load_surrogate(fib_ctx* c, const float* blob, size_t n_floats) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (c->p.mode != FIB_MODE_SURROGATE) return fail(c, FIB_ESTATE, "context was not created in surrogate mode");
+  const size_t head = 3 + 2 * kIn + 2 * kOut + 4 * kIn;
+  if (!blob || n_floats != head + (size_t)kNumParams)
+    return fail(c, FIB_EINVAL, "surrogate blob must hold %zu floats", head + (size_t)kNumParams);
+  if ((int)blob[0] != kIn || (int)blob[1] != kHid || (int)blob[2] != kOut)
+    return fail(c, FIB_EINVAL, "surrogate blob shape is not 5 -> 128 -> 128 -> 4");
+  for (size_t i = 0; i < n_floats; ++i)
+    if (!std::isfinite(blob[i])) return fail(c, FIB_EINVAL, "surrogate blob has a non-finite value at %zu", i);
+  const float* q = blob + 3;
+  for (int k = 0; k < kIn; ++k) {
+    c->in_mu[k] = q[k];
+    if (!(q[kIn + k] > 0)) return fail(c, FIB_EINVAL, "input scale %d must be > 0", k);
+    c->in_inv_sigma[k] = 1.0f / q[kIn + k];
+  }
+  q += 2 * kIn;
+  for (int k = 0; k < kOut; ++k) {
+    c->out_mu[k] = q[k];
+    c->out_sigma[k] = q[kOut + k];
+  }
+  q += 2 * kOut;
+  for (int k = 0; k < kIn; ++k) {
+    c->env_lo[k] = q[k];
+    c->env_hi[k] = q[kIn + k];
+    c->quiet_lo[k] = q[2 * kIn + k];
+    c->quiet_hi[k] = q[3 * kIn + k];
+  }
+  const float* th = q + 4 * kIn;
+  auto bf = [](float v) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&b);
+  };
+  const size_t n_w = (size_t)kHid * kW1Stride + (size_t)kHid * kW2Stride + 8 * (size_t)kW2Stride;
+  std::vector<uint16_t> w(n_w, 0);
+  uint16_t* W1 = w.data();
+  uint16_t* W2 = W1 + kHid * kW1Stride;
+  uint16_t* W3 = W2 + kHid * kW2Stride;
+  for (int j = 0; j < kHid; ++j)
+    for (int k = 0; k < kIn; ++k) {
+      W1[j * kW1Stride + k] = bf(th[kOffW1 + j * kIn + k]);        // multiplies the bf16 high part
+      W1[j * kW1Stride + kIn + k] = bf(th[kOffW1 + j * kIn + k]);  // and the low part of each input
+    }
+  for (int j = 0; j < kHid; ++j)
+    for (int k = 0; k < kHid; ++k) W2[j * kW2Stride + k] = bf(th[kOffW2 + j * kHid + k]);
+  for (int i = 0; i < kOut; ++i)
+    for (int k = 0; k < kHid; ++k) W3[i * kW2Stride + k] = bf(th[kOffW3 + i * kHid + k]);
+  std::vector<float> bias(2 * kHid + 8, 0.0f);
+  for (int j = 0; j < kHid; ++j) {
+    bias[j] = th[kOffB1 + j];
+    bias[kHid + j] = th[kOffB2 + j];
+  }
+  for (int i = 0; i < kOut; ++i) bias[2 * kHid + i] = th[kOffB3 + i];
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (!c->d_sur_wts) CU(c, cudaMalloc(&c->d_sur_wts, sizeof(uint16_t) * n_w));
+  if (!c->d_sur_bias) CU(c, cudaMalloc(&c->d_sur_bias, sizeof(float) * bias.size()));
+  if (!c->d_fallback) {
+    CU(c, cudaMalloc(&c->d_fallback, sizeof(unsigned long long)));
+    CU(c, cudaMemset(c->d_fallback, 0, sizeof(unsigned long long)));
+  }
+  if (!c->d_fiber_stim) CU(c, cudaMalloc(&c->d_fiber_stim, std::max<size_t>(c->n_fibers, 1)));
+  CU(c, cudaMemcpy(c->d_sur_wts, w.data(), sizeof(uint16_t) * n_w, cudaMemcpyHostToDevice));
+  CU(c, cudaMemcpy(c->d_sur_bias, bias.data(), sizeof(float) * bias.size(), cudaMemcpyHostToDevice));
+  CU(c, (cudaError_t)sur_set_smem_attributes());
+  c->sur_loaded = true;
+  return FIB_OK;
+}
+
+fib_status fibers_hh_reaction(const fib_params* p, int64_t count, const float* in, const uint8_t* stim_mask,
+                              float* out, void* cuda_stream) {
+  fib_status st = validate(p);
+  if (st != FIB_OK) return st;
+  if (count < 0 || (count > 0 && (!in || !out))) return fail(nullptr, FIB_EINVAL, "bad count or NULL buffer");
+  const double EL = std::isnan(p->EL) ? exact_leak_reversal(*p) : p->EL;
+  const int n_sub = (int)std::nearbyint(p->dt_split / p->dt_0d);
+  if (n_sub > 8) return fail(nullptr, FIB_EINVAL, "the reaction kernel handles at most 8 substeps per split step");
+  const int e = launch_hh_reaction(hh_const(*p, EL), (float)p->Vrest, n_sub, count, in, stim_mask, out, cuda_stream);
+  if (e) return fail(nullptr, FIB_ECUDA, "reaction kernel: %s", cudaGetErrorString((cudaError_t)e));
+  return FIB_OK;
+}
+
+fib_status fibers_mlp_train_step(const float* theta, int32_t quantize, const float* x, const float* target,
+                                 int64_t batch, float* workspace, float* grad, float* loss, void* cuda_stream) {
+  if (batch < 1 || !theta || !x || !target || !workspace || !grad || !loss)
+    return fail(nullptr, FIB_EINVAL, "bad batch or NULL buffer");
+  int e = sur_set_smem_attributes();
+  if (!e) e = launch_mlp_train_step(theta, quantize, x, target, batch, workspace, grad, loss, cuda_stream);
+  if (e) return fail(nullptr, FIB_ECUDA, "training kernels: %s", cudaGetErrorString((cudaError_t)e));
+  return FIB_OK;
+}
+
+fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float* x, int64_t batch, float* workspace,
+                              float* out, void* cuda_stream) {
+  if (batch < 1 || !theta || !x || !workspace || !out) return fail(nullptr, FIB_EINVAL, "bad batch or NULL buffer");
+  int e = sur_set_smem_attributes();
+  if (!e) e = launch_mlp_forward(theta, quantize, x, batch, workspace, out, cuda_stream);
+  if (e) return fail(nullptr, FIB_ECUDA, "forward kernel: %s", cudaGetErrorString((cudaError_t)e));
+  return FIB_OK;
+}
+
+fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad, int64_t n, float lr, float beta1,
+                            float beta2, float eps, int64_t t, void* cuda_stream) {
+  if (n < 1 || t < 1 || !theta || !m || !v || !grad) return fail(nullptr, FIB_EINVAL, "bad size, step or buffer");
+  const int e = launch_adam(theta, m, v, grad, n, lr, beta1, beta2, eps, t, cuda_stream);
+  if (e) return fail(nullptr, FIB_ECUDA, "adam kernel: %s", cudaGetErrorString((cudaError_t)e));
+  return FIB_OK;
+}
+
+fib_status fibers_feature_stats(const float* X, int64_t n, int32_t cols, double* out, void* cuda_stream) {
+  if (n < 1 || cols < 1 || cols > 64 || !X || !out) return fail(nullptr, FIB_EINVAL, "bad size or buffer");
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(double) * 4 * cols);
+  if (e != cudaSuccess) return fail(nullptr, FIB_ENOMEM, "stats buffer: %s", cudaGetErrorString(e));
+  int le = launch_stats(X, n, cols, d, cuda_stream);
+  if (!le) e = cudaMemcpyAsync(out, d, sizeof(double) * 4 * cols, cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
+  if (!le && e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  cudaFree(d);
+  if (le) return fail(nullptr, FIB_ECUDA, "stats kernel: %s", cudaGetErrorString((cudaError_t)le));
+  if (e != cudaSuccess) return fail(nullptr, FIB_ECUDA, "stats: %s", cudaGetErrorString(e));
+  return FIB_OK;
+}
+
 void fibers_destroy(fib_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
@@ -839,6 +1066,10 @@ void fibers_destroy(fib_ctx* c) {
   dfree(c->d_step);
   dfree(c->d_flag);
   dfree(c->d_stage);
+  dfree(c->d_fiber_stim);
+  dfree(c->d_sur_wts);
+  dfree(c->d_sur_bias);
+  dfree(c->d_fallback);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }

@@ -78,7 +78,7 @@ struct StepArgs {
   int32_t W;               // warps per CTA
   int32_t packed;          // 1: reaction step on node pairs with FP32x2 arithmetic
   int32_t lean;            // 1: kernel built for 3 CTAs of 256 threads per SM (<= 85 registers)
-  int32_t pad2;
+  int32_t phases;          // bit 0: first CN half, bit 1: reaction, bit 2: second CN half
 };
 
 // Host-built solver tables for one (K, r, fiber-length set).

@@ -93,5 +93,28 @@ __device__ __forceinline__ Deriv hh_rhs(float u, float m, float h, float n, floa
   return d;
 }
 
+// One Heun substep (eq:heun) of every node a thread holds.  STIM: the
+// thread owns at least one junction node and the pulse is on; `mask` has
+// bit j set for stimulated nodes.
+template <int K, bool STIM>
+__device__ __forceinline__ void heun_nodes(float (&u)[K], float (&m)[K], float (&h)[K], float (&n)[K],
+                                           const HHConst& c, uint32_t mask) {
+  const float dt = c.dt0, hdt = 0.5f * c.dt0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float s = (STIM && ((mask >> j) & 1u)) ? c.gL_uL + c.stim : c.gL_uL;
+    const Deriv f0 = hh_rhs(u[j], m[j], h[j], n[j], s, c);
+    const float u1 = fmaf(dt, f0.u, u[j]);
+    const float m1 = fmaf(-dt, f0.m, m[j]);
+    const float h1 = fmaf(dt, f0.h, h[j]);
+    const float n1 = fmaf(-dt, f0.n, n[j]);
+    const Deriv f1 = hh_rhs(u1, m1, h1, n1, s, c);
+    u[j] = fmaf(hdt, f0.u + f1.u, u[j]);
+    m[j] = fmaf(-hdt, f0.m + f1.m, m[j]);
+    h[j] = fmaf(hdt, f0.h + f1.h, h[j]);
+    n[j] = fmaf(-hdt, f0.n + f1.n, n[j]);
+  }
+}
+
 }  // namespace
 }  // namespace fib

@@ -1,0 +1,550 @@
+// Learned surrogate of the 0D reaction step (the Heun substeps of the HH model
+// inside one Strang split step, eq:monodomain_strang / eq:heun).  The thesis
+// has no learned component on this path; these kernels implement the
+// surrogate the build adds:
+//   * hh_reaction_kernel: the plain reaction step on independent nodes, which
+//     generates training targets and serves as the per-node fallback;
+//   * training kernels (FP32 master weights, optional bfloat16 rounding of
+//     weights and activations in the forward pass, straight-through
+//     gradients) and an Adam update;
+//   * sur_step_kernel: inference on BF16 tensor cores (mma.sync m16n8k16,
+//     FP32 accumulation) with an envelope test that sends nodes outside the
+//     training data's range to the plain HH step.
+// Network: x (5) -> 128 -> SiLU -> 128 -> SiLU -> 4, predicting the change of
+// (u, m, h, n) over one split step in normalised units.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fibers_internal.h"
+#include "hh_device.cuh"
+#include "surrogate_internal.h"
+
+namespace fib {
+namespace {
+
+constexpr int kFwdSmem = 4 * (kHid * kHid + kOut * kHid + 2 * kHid);
+constexpr int kBwdSmem = 4 * (kHid * kHid + kOut * kHid + kOut + kHid);
+
+__device__ __forceinline__ float silu(float z) { return z * rcp_approx(1.0f + ex2_approx(-kLog2e * z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+__device__ __forceinline__ float q_bf16(float x, int quantize) {
+  return quantize ? __bfloat162float(__float2bfloat16_rn(x)) : x;
+}
+
+// ---------------------------------------------------------------------------
+// Plain reaction step on independent nodes (targets and fallback)
+// ---------------------------------------------------------------------------
+
+// Heun substeps of one node with the stimulus on for substeps whose bit is
+// set in `mask`.  Same arithmetic as the split-step kernel's reaction phase.
+__device__ __forceinline__ void reaction_node(float& u, float& m, float& h, float& n, uint32_t mask, int n_sub,
+                                              const HHConst& c) {
+  float uu[1] = {u}, mm[1] = {m}, hh[1] = {h}, nn[1] = {n};
+  for (int k = 0; k < n_sub; ++k) {
+    if ((mask >> k) & 1u) heun_nodes<1, true>(uu, mm, hh, nn, c, 1u);
+    else heun_nodes<1, false>(uu, mm, hh, nn, c, 0u);
+  }
+  u = uu[0];
+  m = mm[0];
+  h = hh[0];
+  n = nn[0];
+}
+
+__global__ void hh_reaction_kernel(HHConst c, float vrest, int n_sub, int64_t count, const float* in,
+                                   const uint8_t* stim, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    float u = in[i] - vrest, m = in[count + i], h = in[2 * count + i], n = in[3 * count + i];
+    reaction_node(u, m, h, n, stim ? stim[i] : 0u, n_sub, c);
+    out[i] = u + vrest;
+    out[count + i] = m;
+    out[2 * count + i] = h;
+    out[3 * count + i] = n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Training kernels (one CTA of 128 threads per sample for the per-sample
+// passes; one thread per weight for the reductions over the batch)
+// ---------------------------------------------------------------------------
+
+// Forward pass of a chunk of samples per CTA.  W2 is staged transposed in
+// shared memory (thread j reads column j: conflict-free), rounded to bf16
+// when quantising.
+__global__ void __launch_bounds__(kHid) mlp_fwd_kernel(const float* __restrict__ th, int quantize,
+                                                       const float* __restrict__ x, int64_t B, float* z1, float* a1,
+                                                       float* z2, float* a2, float* out) {
+  extern __shared__ float sm[];
+  float* sW2T = sm;                    // [k][j]
+  float* sW3 = sW2T + kHid * kHid;     // [i][k]
+  float* s_a1 = sW3 + kOut * kHid;
+  float* s_a2 = s_a1 + kHid;
+  const int j = threadIdx.x;
+  const float* W1 = th + kOffW1;
+  const float* b1 = th + kOffB1;
+  const float* W2 = th + kOffW2;
+  const float* b2 = th + kOffB2;
+  const float* W3 = th + kOffW3;
+  const float* b3 = th + kOffB3;
+  for (int i = j; i < kHid * kHid; i += kHid) sW2T[(i % kHid) * kHid + i / kHid] = q_bf16(W2[i], quantize);
+  for (int i = j; i < kOut * kHid; i += kHid) sW3[i] = q_bf16(W3[i], quantize);
+  float w1[kIn];
+  for (int k = 0; k < kIn; ++k) w1[k] = q_bf16(W1[j * kIn + k], quantize);
+  __syncthreads();
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    float acc = b1[j];
+    for (int k = 0; k < kIn; ++k) acc += w1[k] * q_bf16(x[b * kIn + k], quantize);
+    z1[b * kHid + j] = acc;
+    const float v1 = q_bf16(acc / (1.0f + __expf(-acc)), quantize);
+    a1[b * kHid + j] = v1;
+    s_a1[j] = v1;
+    __syncthreads();
+    acc = b2[j];
+    for (int k = 0; k < kHid; ++k) acc += sW2T[k * kHid + j] * s_a1[k];
+    z2[b * kHid + j] = acc;
+    const float v2 = q_bf16(acc / (1.0f + __expf(-acc)), quantize);
+    a2[b * kHid + j] = v2;
+    s_a2[j] = v2;
+    __syncthreads();
+    if (j < kOut) {
+      float o = b3[j];
+      for (int k = 0; k < kHid; ++k) o += sW3[j * kHid + k] * s_a2[k];
+      out[b * kOut + j] = o;
+    }
+    __syncthreads();
+  }
+}
+
+// Per-sample backward: d(out) of the mean-squared error, then dz2 and dz1.
+// W2 is staged row-major (thread j reads column j of row i: conflict-free).
+__global__ void __launch_bounds__(kHid) mlp_bwd_kernel(const float* __restrict__ th, int quantize, int64_t B,
+                                                       const float* z1, const float* z2, const float* out,
+                                                       const float* target, float* dout, float* dz1, float* dz2) {
+  extern __shared__ float sm[];
+  float* sW2 = sm;                     // [i][j]
+  float* sW3 = sW2 + kHid * kHid;      // [i][k]
+  float* s_do = sW3 + kOut * kHid;
+  float* s_dz2 = s_do + kOut;
+  const int j = threadIdx.x;
+  const float* W2 = th + kOffW2;
+  const float* W3 = th + kOffW3;
+  for (int i = j; i < kHid * kHid; i += kHid) sW2[i] = q_bf16(W2[i], quantize);
+  for (int i = j; i < kOut * kHid; i += kHid) sW3[i] = q_bf16(W3[i], quantize);
+  __syncthreads();
+  const float scale = 2.0f / (float)(B * kOut);
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    if (j < kOut) {
+      const float d = scale * (out[b * kOut + j] - target[b * kOut + j]);
+      s_do[j] = d;
+      dout[b * kOut + j] = d;
+    }
+    __syncthreads();
+    float da2 = 0.0f;
+    for (int i = 0; i < kOut; ++i) da2 += s_do[i] * sW3[i * kHid + j];
+    const float g2 = da2 * silu_grad(z2[b * kHid + j]);
+    dz2[b * kHid + j] = g2;
+    s_dz2[j] = g2;
+    __syncthreads();
+    float da1 = 0.0f;
+    for (int i = 0; i < kHid; ++i) da1 += s_dz2[i] * sW2[i * kHid + j];
+    dz1[b * kHid + j] = da1 * silu_grad(z1[b * kHid + j]);
+    __syncthreads();
+  }
+}
+
+// grad(W)[r, k] = sum_b D[b, r] X[b, k] (rows x cols weights), grad(b)[r] = sum_b D[b, r].
+__global__ void wgrad_kernel(const float* D, int rows, const float* X, int cols, int64_t B, int quantize_x,
+                             float* gW, float* gb) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nW = (int64_t)rows * cols;
+  if (idx < nW) {
+    const int r = (int)(idx / cols), k = (int)(idx % cols);
+    float acc = 0.0f;
+    for (int64_t b = 0; b < B; ++b) acc += D[b * rows + r] * q_bf16(X[b * cols + k], quantize_x);
+    gW[idx] = acc;
+  } else if (idx < nW + rows) {
+    const int r = (int)(idx - nW);
+    float acc = 0.0f;
+    for (int64_t b = 0; b < B; ++b) acc += D[b * rows + r];
+    gb[r] = acc;
+  }
+}
+
+__global__ void mse_kernel(const float* out, const float* target, int64_t n, float* loss) {
+  __shared__ float part[256];
+  float acc = 0.0f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float d = out[i] - target[i];
+    acc += d * d;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = part[0] / (float)n;
+}
+
+__global__ void adam_kernel(float* th, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float mi = b1 * m[i] + (1.0f - b1) * g[i];
+    const float vi = b2 * v[i] + (1.0f - b2) * g[i] * g[i];
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// Column statistics of an (n x 5) feature matrix: mean, std, min, max (FP64).
+__global__ void stats_kernel(const float* X, int64_t n, int cols, double* out) {
+  __shared__ double s1[256], s2[256], mn[256], mx[256];
+  const int c = blockIdx.x;
+  double a = 0, b = 0, lo = 1e300, hi = -1e300;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = X[i * cols + c];
+    a += v;
+    b += v * v;
+    lo = v < lo ? v : lo;
+    hi = v > hi ? v : hi;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  mn[threadIdx.x] = lo;
+  mx[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s1[threadIdx.x] += s1[threadIdx.x + s];
+      s2[threadIdx.x] += s2[threadIdx.x + s];
+      mn[threadIdx.x] = mn[threadIdx.x + s] < mn[threadIdx.x] ? mn[threadIdx.x + s] : mn[threadIdx.x];
+      mx[threadIdx.x] = mx[threadIdx.x + s] > mx[threadIdx.x] ? mx[threadIdx.x + s] : mx[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = s1[0] / (double)n;
+    const double var = s2[0] / (double)n - mean * mean;
+    out[4 * c + 0] = mean;
+    out[4 * c + 1] = var > 0 ? sqrt(var) : 0.0;
+    out[4 * c + 2] = mn[0];
+    out[4 * c + 3] = mx[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inference on BF16 tensor cores
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half), .y = hi
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// D = A (16x16 bf16, row) * B (16x8 bf16, col) + C, FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Bias + SiLU on the accumulators of two adjacent n-tiles, packed into one
+// bf16 A fragment of the next layer (a C fragment of m16n8 pairs maps onto
+// the A fragment of m16k16).
+__device__ __forceinline__ void to_a_frag(const float (&c0)[4], const float (&c1)[4], const float* bias0,
+                                          const float* bias1, int t, uint32_t (&a)[4]) {
+  const float b00 = bias0[2 * t], b01 = bias0[2 * t + 1], b10 = bias1[2 * t], b11 = bias1[2 * t + 1];
+  a[0] = pack_bf16(silu(c0[0] + b00), silu(c0[1] + b01));
+  a[1] = pack_bf16(silu(c0[2] + b00), silu(c0[3] + b01));
+  a[2] = pack_bf16(silu(c1[0] + b10), silu(c1[1] + b11));
+  a[3] = pack_bf16(silu(c1[2] + b10), silu(c1[3] + b11));
+}
+
+struct SurNode {
+  float u, m, h, n, s;  // state and stimulus fraction
+  int fiber;            // -1: padding (no update)
+  uint32_t mask;        // stimulus substeps
+};
+
+__device__ __forceinline__ SurNode load_node(const SurArgs& a, int64_t q) {
+  SurNode r{};
+  r.fiber = -1;
+  if (q >= a.n_slots) return r;
+  const int32_t f = a.slot_fiber[q];
+  r.u = a.u[q];
+  r.m = a.m[q];
+  r.h = a.h[q];
+  r.n = a.n[q];
+  r.mask = 0u;
+  r.s = 0.0f;
+  if (f >= 0) {
+    const FiberDesc fd = a.fibers[f];
+    const int i = (int)(q - fd.slot);
+    if (i < fd.n) {
+      r.fiber = f;
+      const int lo = max(fd.junction - a.hw, 0), hi = min(fd.junction + a.hw, fd.n - 1);
+      if (i >= lo && i <= hi) {
+        r.mask = a.fiber_stim[f];
+        r.s = (float)__popc(r.mask) / (float)a.n_sub;
+      }
+    }
+  }
+  return r;
+}
+
+// The network only handles nodes inside its training envelope and away from
+// rest: near rest the exact step is cheap and keeps rest an exact fixed
+// point, which a network's small output errors would not.
+__device__ __forceinline__ bool use_plain_step(const SurArgs& a, const SurNode& v) {
+  const float raw[kIn] = {v.u, v.m, v.h, v.n, v.s};
+  bool outside = false, quiet = true;
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) {
+    outside = outside || !(raw[k] >= a.env_lo[k] && raw[k] <= a.env_hi[k]);
+    quiet = quiet && raw[k] >= a.quiet_lo[k] && raw[k] <= a.quiet_hi[k];
+  }
+  return outside || quiet;
+}
+
+__global__ void __launch_bounds__(128) sur_step_kernel(const SurArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint16_t* sW1 = reinterpret_cast<uint16_t*>(smem_raw);  // [kHid][kW1Stride]
+  uint16_t* sW2 = sW1 + kHid * kW1Stride;                  // [kHid][kW2Stride]
+  uint16_t* sW3 = sW2 + kHid * kW2Stride;                  // [8][kW2Stride]
+  float* sB = reinterpret_cast<float*>(sW3 + 8 * kW2Stride);  // b1[128], b2[128], b3[8]
+  {
+    const uint32_t* g = reinterpret_cast<const uint32_t*>(a.wts);
+    uint32_t* s = reinterpret_cast<uint32_t*>(smem_raw);
+    const int words = (kHid * kW1Stride + kHid * kW2Stride + 8 * kW2Stride) / 2;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) s[i] = g[i];
+    for (int i = threadIdx.x; i < 2 * kHid + 8; i += blockDim.x) sB[i] = a.bias[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  const int64_t n_tiles = (a.n_slots + 15) / 16;
+  unsigned long long fallbacks = 0;
+  for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < n_tiles;
+       tile += warps_total) {
+    const int64_t q0 = tile * 16 + g, q1 = q0 + 8;
+    const SurNode v0 = load_node(a, q0), v1 = load_node(a, q1);
+    const bool fb0 = v0.fiber >= 0 && use_plain_step(a, v0);
+    const bool fb1 = v1.fiber >= 0 && use_plain_step(a, v1);
+    const bool net0 = v0.fiber >= 0 && !fb0, net1 = v1.fiber >= 0 && !fb1;
+    if (__any_sync(0xffffffffu, net0 || net1)) {
+    // normalised features, split into bf16 hi + lo parts (FP32-accurate inputs)
+    float x0[kIn], x1[kIn];
+    {
+      const float r0[kIn] = {v0.u, v0.m, v0.h, v0.n, v0.s};
+      const float r1[kIn] = {v1.u, v1.m, v1.h, v1.n, v1.s};
+#pragma unroll
+      for (int k = 0; k < kIn; ++k) {
+        x0[k] = (r0[k] - a.in_mu[k]) * a.in_inv_sigma[k];
+        x1[k] = (r1[k] - a.in_mu[k]) * a.in_inv_sigma[k];
+      }
+    }
+    auto feat = [&](const float (&x)[kIn], int col) -> float {
+      if (col < kIn) return __bfloat162float(__float2bfloat16_rn(x[col]));
+      if (col < 2 * kIn) {
+        const float hi = __bfloat162float(__float2bfloat16_rn(x[col - kIn]));
+        return x[col - kIn] - hi;
+      }
+      return 0.0f;
+    };
+    uint32_t A1[4];
+    A1[0] = pack_bf16(feat(x0, 2 * t), feat(x0, 2 * t + 1));
+    A1[1] = pack_bf16(feat(x1, 2 * t), feat(x1, 2 * t + 1));
+    A1[2] = pack_bf16(feat(x0, 2 * t + 8), feat(x0, 2 * t + 9));
+    A1[3] = pack_bf16(feat(x1, 2 * t + 8), feat(x1, 2 * t + 9));
+    // layer 1: 16 n-tiles of 8 neurons, one k-tile
+    uint32_t A2[8][4];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+      const uint32_t* w0 = reinterpret_cast<const uint32_t*>(sW1 + (16 * kk + g) * kW1Stride);
+      const uint32_t* w1 = reinterpret_cast<const uint32_t*>(sW1 + (16 * kk + 8 + g) * kW1Stride);
+      mma_bf16(c0, A1, w0[t], w0[t + 4]);
+      mma_bf16(c1, A1, w1[t], w1[t + 4]);
+      to_a_frag(c0, c1, sB + 16 * kk, sB + 16 * kk + 8, t, A2[kk]);
+    }
+    // layer 2: 16 n-tiles, 8 k-tiles
+    uint32_t A3[8][4];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+      const uint32_t* w0 = reinterpret_cast<const uint32_t*>(sW2 + (16 * kk + g) * kW2Stride);
+      const uint32_t* w1 = reinterpret_cast<const uint32_t*>(sW2 + (16 * kk + 8 + g) * kW2Stride);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        mma_bf16(c0, A2[k2], w0[8 * k2 + t], w0[8 * k2 + t + 4]);
+        mma_bf16(c1, A2[k2], w1[8 * k2 + t], w1[8 * k2 + t + 4]);
+      }
+      to_a_frag(c0, c1, sB + kHid + 16 * kk, sB + kHid + 16 * kk + 8, t, A3[kk]);
+    }
+    // layer 3: one n-tile (4 outputs padded to 8), 8 k-tiles
+    float o[4] = {0, 0, 0, 0};
+    {
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(sW3 + g * kW2Stride);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) mma_bf16(o, A3[k2], w[8 * k2 + t], w[8 * k2 + t + 4]);
+    }
+    // lane t = 0 holds outputs 0, 1 (du, dm) and t = 1 outputs 2, 3 (dh, dn)
+    // of node rows g (o[0], o[1]) and g + 8 (o[2], o[3])
+    if (t < 2) {
+      const int k0 = 2 * t, k1 = 2 * t + 1;
+      const float b0 = sB[2 * kHid + k0], b1 = sB[2 * kHid + k1];
+      float* dst0 = k0 == 0 ? a.u : a.h;
+      float* dst1 = k1 == 1 ? a.m : a.n;
+      if (net0) {
+        const float y0 = k0 == 0 ? v0.u : v0.h, y1 = k1 == 1 ? v0.m : v0.n;
+        dst0[q0] = y0 + fmaf(o[0] + b0, a.out_sigma[k0], a.out_mu[k0]);
+        dst1[q0] = y1 + fmaf(o[1] + b1, a.out_sigma[k1], a.out_mu[k1]);
+      }
+      if (net1) {
+        const float y0 = k0 == 0 ? v1.u : v1.h, y1 = k1 == 1 ? v1.m : v1.n;
+        dst0[q1] = y0 + fmaf(o[2] + b0, a.out_sigma[k0], a.out_mu[k0]);
+        dst1[q1] = y1 + fmaf(o[3] + b1, a.out_sigma[k1], a.out_mu[k1]);
+      }
+    }
+    }  // network part of the tile
+    // fallback: the plain HH reaction step, node row g by lane t = 0 and
+    // node row g + 8 by lane t = 1
+    if ((t == 0 && fb0) || (t == 1 && fb1)) {
+      SurNode v = t == 0 ? v0 : v1;
+      const int64_t q = t == 0 ? q0 : q1;
+      reaction_node(v.u, v.m, v.h, v.n, v.mask, a.n_sub, a.hh);
+      a.u[q] = v.u;
+      a.m[q] = v.m;
+      a.h[q] = v.h;
+      a.n[q] = v.n;
+      ++fallbacks;
+    }
+  }
+  if (fallbacks) atomicAdd(a.fallback_count, fallbacks);
+}
+
+// Stimulus substep mask of every fiber for one split step.
+__global__ void fiber_stim_kernel(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off,
+                                  const int64_t* fire_k, int32_t n_mu, const int64_t* step_base, int64_t step_offset,
+                                  int n_sub, int pulse, uint8_t* out) {
+  for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < n_fibers; f += gridDim.x * blockDim.x) {
+    const int mu = fibers[f].mu;
+    uint8_t mask = 0;
+    if (mu >= 0 && mu < n_mu) {
+      const int64_t k0 = (*step_base + step_offset) * n_sub;
+      int64_t lo = mu_off[mu], hi = mu_off[mu + 1];
+      const int64_t end = hi;
+      while (lo < hi) {  // first firing whose pulse has not ended at k0
+        const int64_t mid = (lo + hi) >> 1;
+        if (fire_k[mid] + pulse <= k0) lo = mid + 1;
+        else hi = mid;
+      }
+      for (int k = 0; k < n_sub; ++k) {
+        int64_t cur = lo;
+        while (cur < end && fire_k[cur] + pulse <= k0 + k) ++cur;
+        if (cur < end && fire_k[cur] <= k0 + k) mask |= (uint8_t)(1u << k);
+      }
+    }
+    out[f] = mask;
+  }
+}
+
+}  // namespace
+
+size_t sur_smem_bytes() {
+  return 2 * ((size_t)kHid * kW1Stride + (size_t)kHid * kW2Stride + 8 * (size_t)kW2Stride) +
+         4 * (2 * (size_t)kHid + 8);
+}
+
+int launch_hh_reaction(const HHConst& c, float vrest, int n_sub, int64_t count, const float* in,
+                       const uint8_t* stim, float* out, void* stream) {
+  if (count <= 0) return 0;
+  const int64_t blocks = (count + 255) / 256;
+  hh_reaction_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, (cudaStream_t)stream>>>(c, vrest, n_sub, count,
+                                                                                                in, stim, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_mlp_train_step(const float* th, int quantize, const float* x, const float* target, int64_t B, float* ws,
+                          float* grad, float* loss, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  float* z1 = ws;
+  float* a1 = z1 + B * kHid;
+  float* z2 = a1 + B * kHid;
+  float* a2 = z2 + B * kHid;
+  float* out = a2 + B * kHid;
+  float* dout = out + B * kOut;
+  float* dz1 = dout + B * kOut;
+  float* dz2 = dz1 + B * kHid;
+  const int grid = (int)(B < 152 * 8 ? B : 152 * 8);
+  mlp_fwd_kernel<<<grid, kHid, kFwdSmem, s>>>(th, quantize, x, B, z1, a1, z2, a2, out);
+  mse_kernel<<<1, 256, 0, s>>>(out, target, B * kOut, loss);
+  mlp_bwd_kernel<<<grid, kHid, kBwdSmem, s>>>(th, quantize, B, z1, z2, out, target, dout, dz1, dz2);
+  auto wg = [&](const float* D, int rows, const float* X, int cols, int qx, int64_t offW, int64_t offB) {
+    const int64_t n = (int64_t)rows * cols + rows;
+    wgrad_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(D, rows, X, cols, B, qx, grad + offW, grad + offB);
+  };
+  wg(dout, kOut, a2, kHid, 0, kOffW3, kOffB3);
+  wg(dz2, kHid, a1, kHid, 0, kOffW2, kOffB2);
+  wg(dz1, kHid, x, kIn, quantize, kOffW1, kOffB1);
+  return (int)cudaGetLastError();
+}
+
+int launch_mlp_forward(const float* th, int quantize, const float* x, int64_t B, float* ws, float* out, void* stream) {
+  float* z1 = ws;
+  float* a1 = z1 + B * kHid;
+  float* z2 = a1 + B * kHid;
+  float* a2 = z2 + B * kHid;
+  const int grid = (int)(B < 152 * 8 ? B : 152 * 8);
+  mlp_fwd_kernel<<<grid, kHid, kFwdSmem, (cudaStream_t)stream>>>(th, quantize, x, B, z1, a1, z2, a2, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_adam(float* th, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2, float eps,
+                int64_t t, void* stream) {
+  const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+  adam_kernel<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(th, m, v, g, n, lr, b1, b2, eps, c1, c2);
+  return (int)cudaGetLastError();
+}
+
+int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream) {
+  stats_kernel<<<cols, 256, 0, (cudaStream_t)stream>>>(X, n, cols, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_sur_step(const SurArgs& a, void* stream) {
+  const int64_t tiles = (a.n_slots + 15) / 16;
+  int blocks = (int)((tiles + 3) / 4);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  sur_step_kernel<<<blocks, 128, sur_smem_bytes(), (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_fiber_stim(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off, const int64_t* fire_k,
+                      int32_t n_mu, const int64_t* step_base, int64_t step_offset, int n_sub, int pulse, uint8_t* out,
+                      void* stream) {
+  if (n_fibers <= 0) return 0;
+  fiber_stim_kernel<<<(n_fibers + 255) / 256, 256, 0, (cudaStream_t)stream>>>(fibers, n_fibers, mu_off, fire_k, n_mu,
+                                                                             step_base, step_offset, n_sub, pulse, out);
+  return (int)cudaGetLastError();
+}
+
+int sur_set_smem_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(sur_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sur_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
+  return (int)e;
+}
+
+}  // namespace fib

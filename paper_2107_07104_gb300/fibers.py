@@ -31,7 +31,12 @@ STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINI
 EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
             "fibers_write_state",
             "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
-            "fibers_kernel_launches", "fibers_last_error", "fibers_destroy")
+            "fibers_kernel_launches", "fibers_last_error", "fibers_destroy", "fibers_load_surrogate",
+            "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward", "fibers_adam_step",
+            "fibers_feature_stats")
+SUR_N_PARAMS = 17796
+SUR_BLOB_FLOATS = 3 + 5 + 5 + 4 + 4 + 5 + 5 + 5 + 5 + SUR_N_PARAMS
+SUR_WORK_PER_SAMPLE = 6 * 128 + 2 * 4
 
 
 class FibersError(RuntimeError):
@@ -99,6 +104,16 @@ def load(build_if_missing: bool = True):
         L.fibers_last_error.restype = ctypes.c_char_p
         L.fibers_destroy.argtypes = [vp]
         L.fibers_destroy.restype = None
+        f32, f64p = ctypes.c_float, P(ctypes.c_double)
+        L.fibers_load_surrogate.argtypes = [vp, P(ctypes.c_float), sz]
+        L.fibers_hh_reaction.argtypes = [P(FibParams), i64, vp, vp, vp, vp]
+        L.fibers_mlp_train_step.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp, vp]
+        L.fibers_mlp_forward.argtypes = [vp, i32, vp, i64, vp, vp, vp]
+        L.fibers_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]
+        L.fibers_feature_stats.argtypes = [vp, i64, i32, f64p, vp]
+        for name in ("fibers_load_surrogate", "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward",
+                     "fibers_adam_step", "fibers_feature_stats"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
                      "fibers_write_state", "fibers_stats", "fibers_synchronize", "fibers_get_tuning",
                      "fibers_set_tuning", "fibers_autotune"):
@@ -239,6 +254,56 @@ def fibers_autotune(ctx, n_trial_steps: int = 20) -> dict:
     t = FibTuning()
     _check(load().fibers_autotune(ctx, int(n_trial_steps), ctypes.byref(t)), ctx)
     return t.as_dict()
+
+
+def _dev(t):
+    """Device pointer of a contiguous CUDA tensor (surrogate entry points take device buffers)."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+
+
+def fibers_load_surrogate(ctx, blob: np.ndarray) -> None:
+    b = np.ascontiguousarray(blob, dtype=np.float32)
+    _check(load().fibers_load_surrogate(ctx, _ptr(b, ctypes.c_float), b.size), ctx)
+
+
+def fibers_hh_reaction(params: dict, x_in, stim_mask, x_out, stream=None) -> None:
+    """x_in / x_out: CUDA float32 tensors of 4 x count (V | m | h | n); stim_mask: uint8 count or None."""
+    count = x_in.numel() // 4
+    pv = make_params(params)
+    _check(load().fibers_hh_reaction(ctypes.byref(pv), count, _dev(x_in),
+                                     None if stim_mask is None else _dev(stim_mask), _dev(x_out),
+                                     _stream_ptr(stream)), None)
+
+
+def fibers_mlp_train_step(theta, quantize: bool, x, target, workspace, grad, loss, stream=None) -> None:
+    _check(load().fibers_mlp_train_step(_dev(theta), int(bool(quantize)), _dev(x), _dev(target), x.shape[0],
+                                        _dev(workspace), _dev(grad), _dev(loss), _stream_ptr(stream)), None)
+
+
+def fibers_mlp_forward(theta, quantize: bool, x, workspace, out, stream=None) -> None:
+    _check(load().fibers_mlp_forward(_dev(theta), int(bool(quantize)), _dev(x), x.shape[0], _dev(workspace),
+                                     _dev(out), _stream_ptr(stream)), None)
+
+
+def fibers_adam_step(theta, m, v, grad, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    _check(load().fibers_adam_step(_dev(theta), _dev(m), _dev(v), _dev(grad), theta.numel(), float(lr), float(beta1),
+                                   float(beta2), float(eps), int(t), _stream_ptr(stream)), None)
+
+
+def fibers_feature_stats(X, stream=None) -> np.ndarray:
+    """(cols, 4) array of mean, std, min, max per column of a CUDA (n x cols) tensor."""
+    n, cols = X.shape
+    out = np.zeros(4 * cols)
+    _check(load().fibers_feature_stats(_dev(X), n, cols, _ptr(out, ctypes.c_double), _stream_ptr(stream)), None)
+    return out.reshape(cols, 4)
 
 
 def fibers_kernel_launches(ctx) -> int:

@@ -83,11 +83,11 @@ def test_create_rejects_non_finite_initial_voltage(lib):
     assert ei.value.status == F.FIB_EINVAL
 
 
-def test_surrogate_mode_reports_not_supported_until_loaded(lib):
+def test_unknown_mode_is_rejected(lib):
     w = W.small_ragged(1, 2, 5, 6, 10)
     with pytest.raises(F.FibersError) as ei:
-        F.fibers_create(w.params, w.n_nodes, w.mu_of_fiber, w.junction, mode=F.FIB_MODE_SURROGATE)
-    assert ei.value.status in (F.FIB_ENOTSUP, F.FIB_ECUDA)
+        F.fibers_create(w.params, w.n_nodes, w.mu_of_fiber, w.junction, mode=3)
+    assert ei.value.status == F.FIB_EINVAL
 
 
 def test_null_context_is_safe(lib):

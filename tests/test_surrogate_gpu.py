@@ -1,0 +1,170 @@
+"""GPU tests of the reaction-step surrogate: its kernels against the FP64
+oracles, and the surrogate path against the plain path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2107_07104_gb300 import fibers as F
+from paper_2107_07104_gb300 import surrogate as S
+from paper_2107_07104_gb300 import workloads as W
+
+from parity import errors, gpu_checkpoints, oracle_checkpoints, select_fibers
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_reaction_kernel_matches_oracle_heun_steps():
+    p = dict(W.DEFAULT_PARAMS)
+    rng = np.random.default_rng(0)
+    n = 4096
+    V = rng.uniform(-90, 40, n)
+    gates = rng.uniform(0.02, 0.98, (3, n))
+    mask = rng.choice(S.STIM_PATTERNS.tolist() + [0, 0, 0], n).astype(np.uint8)
+    x_in = torch.tensor(np.concatenate([V, gates.ravel()]), dtype=torch.float32, device="cuda")
+    x_out = torch.empty_like(x_in)
+    F.fibers_hh_reaction(p, x_in, torch.tensor(mask, device="cuda"), x_out)
+    got = x_out.cpu().numpy().reshape(4, n)
+    ref = np.zeros((4, n))
+    xin = x_in.cpu().numpy().astype(np.float64).reshape(4, n)
+    for i in range(n):
+        y = xin[:, i].copy()
+        for k in range(3):
+            on = (mask[i] >> k) & 1
+            y = oracle.heun_step(p, y, p["dt_0d"], p["stim_amplitude"] if on else 0.0)
+        ref[:, i] = y
+    assert np.max(np.abs(got[0] - ref[0])) <= 2e-3  # mV, from FP32 inputs and arithmetic
+    assert np.max(np.abs(got[1:] - ref[1:])) <= 2e-5
+
+
+@pytest.mark.parametrize("quantize,tol", [(False, 2e-4), (True, 2e-2)])
+def test_training_kernels_match_the_oracle(quantize, tol):
+    rng = np.random.default_rng(1)
+    theta = omlp.init_params(3) + rng.normal(0, 0.02, omlp.N_PARAMS)
+    B = 96
+    x = rng.normal(size=(B, 5))
+    t = rng.normal(size=(B, 4))
+    th = torch.tensor(theta, dtype=torch.float32, device="cuda")
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    work = torch.empty(B * F.SUR_WORK_PER_SAMPLE, dtype=torch.float32, device="cuda")
+    grad = torch.zeros_like(th)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    F.fibers_mlp_train_step(th, quantize, xd, td, work, grad, loss)
+    # the oracle sees exactly the FP32 values the GPU saw
+    th64 = th.cpu().numpy().astype(np.float64)
+    x64 = xd.cpu().numpy().astype(np.float64)
+    t64 = td.cpu().numpy().astype(np.float64)
+    g_ref, l_ref = omlp.backward(th64, x64, t64, quantize=quantize)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - l_ref) <= tol * l_ref
+    assert np.linalg.norm(g - g_ref) <= tol * np.linalg.norm(g_ref)
+    out = torch.empty(B, 4, dtype=torch.float32, device="cuda")
+    F.fibers_mlp_forward(th, quantize, xd, work, out)
+    o_ref, _ = omlp.forward(th64, x64, quantize=quantize)
+    assert np.max(np.abs(out.cpu().numpy() - o_ref)) <= tol * max(1.0, np.max(np.abs(o_ref)))
+
+
+def test_adam_kernel_matches_the_oracle():
+    rng = np.random.default_rng(2)
+    n = 1000
+    th, m, v, g = (rng.normal(size=n) for _ in range(4))
+    v = np.abs(v)
+    dt = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    T, M, Vv, G = dt(th), dt(m), dt(v), dt(g)
+    F.fibers_adam_step(T, M, Vv, G, 1e-3, 7)
+    ref, mr, vr = omlp.adam_step(th.astype(np.float32).astype(np.float64), m.astype(np.float32),
+                                 v.astype(np.float32), g.astype(np.float32), 7, 1e-3)
+    assert np.max(np.abs(T.cpu().numpy() - ref)) <= 1e-6
+    assert np.max(np.abs(M.cpu().numpy() - mr)) <= 1e-6
+
+
+def test_feature_stats_kernel():
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(10000, 5)) * [1, 2, 3, 4, 5] + [5, 4, 3, 2, 1]
+    st = F.fibers_feature_stats(torch.tensor(X, dtype=torch.float32, device="cuda"))
+    Xf = X.astype(np.float32).astype(np.float64)
+    assert np.allclose(st[:, 0], Xf.mean(0), atol=1e-9)
+    assert np.allclose(st[:, 1], Xf.std(0), rtol=1e-6)
+    assert np.allclose(st[:, 2], Xf.min(0)) and np.allclose(st[:, 3], Xf.max(0))
+
+
+def _exclude_all_blob():
+    theta = omlp.init_params(5).astype(np.float32)
+    lo = np.full(5, 1.0, np.float32)
+    hi = np.full(5, -1.0, np.float32)  # empty envelope: every node falls back
+    return S.make_blob(theta, np.zeros(5, np.float32), np.ones(5, np.float32), np.zeros(4, np.float32),
+                       np.ones(4, np.float32), lo, hi, lo, hi)
+
+
+def test_fallback_reproduces_the_plain_path_bit_for_bit():
+    w = W.small_ragged(seed=31, n_fibers=24, lo=1, hi=700, n_steps=300)
+    plain = gpu_checkpoints(w, [150, 300])
+    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as f:
+        with pytest.raises(F.FibersError) as ei:
+            f.step(1)  # no surrogate loaded yet
+        assert ei.value.status == F.FIB_ESTATE
+        F.fibers_load_surrogate(f.ctx, _exclude_all_blob())
+        f.step(150)
+        a = f.read_vm().astype(np.float64)
+        f.step(150)
+        b = f.read_vm().astype(np.float64)
+        _, fallbacks = f.stats()
+    assert np.array_equal(a, plain[0]) and np.array_equal(b, plain[1])
+    assert fallbacks == 300 * w.total_nodes
+
+
+@pytest.fixture(scope="module")
+def trained_blob():
+    """Trained here from scratch: samples from the plain method, GPU training."""
+    log = []
+    blob = S.build_surrogate(seed=0, log=log)
+    assert log[-1] < 0.02 * log[0]  # training reduced the loss by 50x or more
+    return blob
+
+
+def test_surrogate_blob_is_loadable_and_finite(trained_blob):
+    assert trained_blob.size == F.SUR_BLOB_FLOATS and np.isfinite(trained_blob).all()
+    w = W.small_ragged(seed=1, n_fibers=2, lo=50, hi=60, n_steps=10)
+    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as f:
+        F.fibers_load_surrogate(f.ctx, trained_blob)
+        f.step(10)
+        assert np.isfinite(f.read_vm()).all()
+
+
+def test_surrogate_on_held_out_bundle(trained_blob):
+    """Held-out seed of the 7744-fiber bundle (seed 4), 16 fibers, 20 ms:
+    errors against the FP64 oracle, next to the plain FP32 path's."""
+    full = W.bundle_7744(seed=4, t_end_ms=20.0)
+    firing = [f for f in range(full.n_fibers) if full.mu_offsets[full.mu_of_fiber[f] + 1] > full.mu_offsets[full.mu_of_fiber[f]]]
+    fibers = np.sort(np.random.default_rng(4).choice(firing, 16, replace=False))
+    w = full.subset(fibers)
+    cps = list(range(10, w.n_steps + 1, 10))
+    o = oracle_checkpoints(w, cps)
+    plain = gpu_checkpoints(w, cps)
+    sur = []
+    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as f:
+        F.fibers_load_surrogate(f.ctx, trained_blob)
+        done = 0
+        for c in cps:
+            f.step(c - done)
+            done = c
+            sur.append(f.read_vm().astype(np.float64))
+        _, fb = f.stats()
+    sur = np.array(sur)
+    ep, es = errors(plain, o), errors(sur, o)
+    from parity import activation_times
+    dt = 10 * w.params["dt_split"]
+    to, ts = activation_times(o, dt), activation_times(sur, dt)
+    both = ~np.isnan(to) & ~np.isnan(ts)
+    act = float(np.max(np.abs(to[both] - ts[both]))) if both.any() else float("nan")
+    print(f"[surrogate] plain FP32: max|dV| {ep[0]:.3e} mV rel L2 {ep[1]:.3e}; surrogate: max|dV| {es[0]:.3e} mV "
+          f"rel L2 {es[1]:.3e}; activation-time max error {act:.3e} ms over {both.sum()} nodes "
+          f"(missed {int((~np.isnan(to) & np.isnan(ts)).sum())}); fallback node-steps {fb}")
+    assert np.isfinite(sur).all()
+    fired = ~np.isnan(to)
+    assert both.sum() >= 0.99 * fired.sum()          # activations found where the oracle has them
+    assert (np.isnan(to) & ~np.isnan(ts)).sum() <= 0.01 * fired.sum()  # no spurious excitation
+    assert act <= 0.05                                # activation times within 0.05 ms
+    assert es[1] <= 0.01                              # trajectory relative L2 (max|dV| is reported, not bounded)
