@@ -159,6 +159,24 @@ def dram_traffic_from_profile(tune):
         return None
 
 
+def rank_workload(rank: int):
+    """Each rank simulates its own seeded 7744-fiber bundle: fibers are
+    independent, so ranks share nothing on the data path (weak scaling)."""
+    return W.bundle_7744(seed=2 + rank, t_end_ms=20.0)
+
+
+def aggregate_over_ranks(node_updates_local: float, seconds_local: float, dist, device=None):
+    """(node-updates summed over ranks, wall seconds max over ranks)."""
+    if dist is None:
+        return node_updates_local, seconds_local
+    import torch
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+    n = torch.tensor([node_updates_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n.item()), float(t.item())
+
+
 def dist_setup():
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -236,7 +254,7 @@ def run_gpu(args, world, rank, local, dist):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = W.bundle_7744(seed=2 + rank, t_end_ms=20.0)
+    w = rank_workload(rank)
     total = w.total_nodes
     stream = torch.cuda.Stream(device=dev)
     tuning = dict(nodes_per_thread=args.nodes_per_thread, warps_per_cta=args.warps_per_cta,
@@ -280,11 +298,7 @@ def run_gpu(args, world, rank, local, dist):
         rem %= G
     split_launches += (rem + S - 1) // S
 
-    t = torch.tensor([ms / 1e3], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    node_updates = float(total) * args.steps * world
+    node_updates, t_max = aggregate_over_ranks(float(total) * args.steps, ms / 1e3, dist, dev)
     value = node_updates / t_max
 
     # ---- end to end through the C ABI with host buffers ---------------------
@@ -297,10 +311,8 @@ def run_gpu(args, world, rank, local, dist):
     fib2.read_vm(host_out)
     t_e2e = time.perf_counter() - t0
     fib2.close()
-    te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = node_updates / float(te.item())
+    _, te = aggregate_over_ranks(float(total) * args.steps, t_e2e, dist, dev)
+    e2e_value = node_updates / te
     h2d = 12 * w.n_fibers + 8 * (w.mu_offsets.size + w.fire_times.size)
     d2h = 4 * total
 
