@@ -339,6 +339,7 @@ def run_gpu(args, world, rank, local, dist):
                          f"({dt:.1f} s of FP64 oracle on {cores} threads)"}
     clocks = clk.summary()
     sur = None if args.no_surrogate else surrogate_leg(args, w, tune, stream, dev, total, per_gpu_rate)
+    adaptive = None if args.no_adaptive else adaptive_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
@@ -367,6 +368,7 @@ def run_gpu(args, world, rank, local, dist):
         "clocks": clocks,
         "finite": finite,
         "surrogate": sur,
+        "adaptive": adaptive,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -434,6 +436,41 @@ def surrogate_leg(args, w, tune, stream, dev, total, plain_rate):
             "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}
 
 
+def adaptive_leg(args, w, tune, stream, dev, total, plain_rate):
+    """The same bundle with adaptive computation: node-updates/s counted over
+    all nodes (the simulated work), the share of fiber-steps skipped, and the
+    agreement with the plain path at the end of the timed region."""
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+    wa = w.with_steps(w.n_steps)
+    wa.params = dict(w.params)
+    wa.params["flags"] = F.FIB_FLAG_ADAPTIVE
+    fib = F.Fibers.from_workload(wa, tuning=tune, stream=stream)
+    fib.step(args.warmup)
+    fib.synchronize()
+    s0 = F.fibers_adaptive_stats(fib.ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    fib.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    s1 = F.fibers_adaptive_stats(fib.ctx)
+    va = fib.read_vm().astype(np.float64)
+    fib.close()
+    with F.Fibers.from_workload(w, tuning=tune, stream=stream) as ref:
+        ref.step(args.warmup + args.steps)
+        vp = ref.read_vm().astype(np.float64)
+    rate = float(total) * args.steps / (ms / 1e3)
+    return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
+            "skipped_fiber_step_fraction": (s1 - s0) / float(w.n_fibers * args.steps),
+            "equilibrium_test": "every component of every node changed <= 1e-5 relative over a launch's last "
+                                "split step, and no pulse due in the next launch",
+            "max_abs_mv_vs_plain_fp32_at_end": float(np.max(np.abs(va - vp)))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +488,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -64,6 +64,17 @@ enum {
   FIB_MODE_SURROGATE = 2     /* reaction step by a learned MLP with HH fallback */
 };
 
+/* Flags (fib_params.flags). */
+enum {
+  /* Adaptive computation (sec:adaptive_computation_for_fiber_based): a fiber
+   * whose every node passed the thesis's equilibrium test over the last split
+   * step of a kernel launch (each of V, m, h, n changed by at most 1e-5
+   * relative) and whose motor unit has no stimulus pulse overlapping the next
+   * launch is not computed during that launch (steps_per_launch split steps).
+   * All fibers start active.  Not available with FIB_MODE_SURROGATE. */
+  FIB_FLAG_ADAPTIVE = 1
+};
+
 /* Model and discretisation parameters (sec:subcelullar_model, eq:monodomain,
  * eq:monodomain_strang).  ENa, EK and EL are absolute reversal potentials;
  * EL = NaN asks the library to derive it so that (Vrest, m_inf, h_inf, n_inf)
@@ -80,7 +91,7 @@ typedef struct {
   double stim_amplitude, stim_duration;
   int32_t stim_half_width;
   int32_t mode;     /* FIB_MODE_* */
-  int32_t flags;    /* reserved, must be 0 */
+  int32_t flags;    /* FIB_FLAG_* bits (0: none) */
   int32_t reserved; /* must be 0 */
 } fib_params;
 
@@ -179,6 +190,10 @@ fib_status fibers_write_state(fib_ctx* ctx, const float* in, size_t count, int32
 /* Index of the next split step, and nodes handled by the fallback path in
  * surrogate mode (0 otherwise).  Synchronises. */
 fib_status fibers_stats(fib_ctx* ctx, int64_t* steps_done, int64_t* fallback_nodes);
+
+/* Fiber-steps the adaptive scheme skipped so far (0 without
+ * FIB_FLAG_ADAPTIVE).  Synchronises. */
+fib_status fibers_adaptive_stats(fib_ctx* ctx, int64_t* skipped_fiber_steps);
 
 /* Waits for all enqueued work and reports device-side errors. */
 fib_status fibers_synchronize(fib_ctx* ctx);

@@ -58,6 +58,8 @@ struct fib_ctx {
 
   int64_t* d_step = nullptr;
   int32_t* d_flag = nullptr;
+  uint8_t* d_quiet = nullptr;               // adaptive: per-fiber equilibrium flag
+  unsigned long long* d_skipped = nullptr;  // adaptive: fiber-steps skipped
   int64_t next_step = 0;
   int64_t launches = 0;
 
@@ -142,7 +144,10 @@ fib_status validate(const fib_params* p) {
     return fail(nullptr, FIB_EINVAL, "stim_half_width must be in [0, 8]");
   if (p->mode != FIB_MODE_FP32 && p->mode != FIB_MODE_FP64_THOMAS && p->mode != FIB_MODE_SURROGATE)
     return fail(nullptr, FIB_EINVAL, "unknown mode %d", p->mode);
-  if (p->flags != 0 || p->reserved != 0) return fail(nullptr, FIB_EINVAL, "flags and reserved must be 0");
+  if ((p->flags & ~FIB_FLAG_ADAPTIVE) != 0 || p->reserved != 0)
+    return fail(nullptr, FIB_EINVAL, "unknown flags or nonzero reserved field");
+  if ((p->flags & FIB_FLAG_ADAPTIVE) && p->mode == FIB_MODE_SURROGATE)
+    return fail(nullptr, FIB_EINVAL, "adaptive computation is not available in surrogate mode");
   const double q0 = p->dt_split / p->dt_0d, q1 = 0.5 * p->dt_split / p->dt_1d;
   const double r0 = std::nearbyint(q0), r1 = std::nearbyint(q1);
   if (r0 < 1 || r1 < 1 || std::fabs(q0 - r0) > 1e-9 * q0 || std::fabs(q1 - r1) > 1e-9 * q1)
@@ -386,6 +391,11 @@ StepArgs make_args(fib_ctx* c) {
   a.packed = c->tune.reaction_pairs == 2 ? 1 : 0;
   a.lean = c->tune.ctas_per_sm == 3 ? 1 : 0;
   a.phases = 7;
+  a.adaptive = (c->p.flags & FIB_FLAG_ADAPTIVE) ? 1 : 0;
+  a.quiet = c->d_quiet;
+  a.skipped = c->d_skipped;
+  a.eq_tol = 1e-5f;
+  a.vrest = (float)c->p.Vrest;
   return a;
 }
 
@@ -460,7 +470,9 @@ fib_status gather_state(fib_ctx* c, float* dst) {
 }
 
 // Fills the padded layout from a compact (u|m|h|n) device buffer (bit-exact).
+// A replaced state is re-tested by the adaptive scheme: all fibers active.
 fib_status scatter_state(fib_ctx* c, const float* src) {
+  if (c->d_quiet) CU(c, cudaMemsetAsync(c->d_quiet, 0, std::max<size_t>(c->n_fibers, 1), c->stream));
   fib_status st = check_launch(c, launch_fill_layout(c->d_fibers, c->n_fibers, st_u(c), st_m(c), st_h(c), st_n(c),
                                                      nullptr, (float)c->p.Vrest, (float)c->m0, (float)c->h0,
                                                      (float)c->n0, c->stream),
@@ -618,6 +630,13 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
         (e = cudaMalloc(&cx->d_flag, sizeof(int32_t))) != cudaSuccess ||
         (e = cudaMemset(cx->d_step, 0, sizeof(int64_t))) != cudaSuccess ||
         (e = cudaMemset(cx->d_flag, 0, sizeof(int32_t))) != cudaSuccess)
+      st = fail(cx, e == cudaErrorMemoryAllocation ? FIB_ENOMEM : FIB_ECUDA, "allocation: %s", cudaGetErrorString(e));
+  }
+  if (st == FIB_OK && (p->flags & FIB_FLAG_ADAPTIVE)) {
+    if ((e = cudaMalloc(&cx->d_quiet, std::max<size_t>(cx->n_fibers, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&cx->d_skipped, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(cx->d_quiet, 0, std::max<size_t>(cx->n_fibers, 1))) != cudaSuccess ||
+        (e = cudaMemset(cx->d_skipped, 0, sizeof(unsigned long long))) != cudaSuccess)
       st = fail(cx, e == cudaErrorMemoryAllocation ? FIB_ENOMEM : FIB_ECUDA, "allocation: %s", cudaGetErrorString(e));
   }
   float* d_vm0 = nullptr;
@@ -802,6 +821,16 @@ fib_status fibers_stats(fib_ctx* c, int64_t* steps_done, int64_t* fallback_nodes
     if (c->d_fallback) CU(c, cudaMemcpy(&fb, c->d_fallback, sizeof(fb), cudaMemcpyDeviceToHost));
     *fallback_nodes = (int64_t)fb;
   }
+  return check_flag(c);
+}
+
+fib_status fibers_adaptive_stats(fib_ctx* c, int64_t* skipped) {
+  if (!c || !skipped) return fail(c, FIB_EINVAL, "ctx or output is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  CU(c, cudaStreamSynchronize(c->stream));
+  unsigned long long v = 0;
+  if (c->d_skipped) CU(c, cudaMemcpy(&v, c->d_skipped, sizeof(v), cudaMemcpyDeviceToHost));
+  *skipped = (int64_t)v;
   return check_flag(c);
 }
 
@@ -1065,6 +1094,8 @@ void fibers_destroy(fib_ctx* c) {
   dfree(c->d_fire_k);
   dfree(c->d_step);
   dfree(c->d_flag);
+  dfree(c->d_quiet);
+  dfree(c->d_skipped);
   dfree(c->d_stage);
   dfree(c->d_fiber_stim);
   dfree(c->d_sur_wts);

@@ -79,6 +79,12 @@ struct StepArgs {
   int32_t packed;          // 1: reaction step on node pairs with FP32x2 arithmetic
   int32_t lean;            // 1: kernel built for 3 CTAs of 256 threads per SM (<= 85 registers)
   int32_t phases;          // bit 0: first CN half, bit 1: reaction, bit 2: second CN half
+  // adaptive computation: skip fibers in equilibrium with no pulse due
+  uint8_t* quiet;          // per fiber: 1 = passed the equilibrium test at the end of its last launch
+  unsigned long long* skipped;  // fiber-steps skipped
+  int32_t adaptive;
+  float eq_tol;            // relative change that still counts as equilibrium
+  float vrest;             // resting potential (the test uses V = u + Vrest)
 };
 
 // Host-built solver tables for one (K, r, fiber-length set).
@@ -112,7 +118,7 @@ int launch_scatter(const FiberDesc* fibers, int32_t n_fibers, const float* src, 
 int launch_fill_layout(const FiberDesc* fibers, int32_t n_fibers, float* u, float* m, float* h,
                        float* n, const float* vm0_compact, float vrest, float m0, float h0, float n0,
                        void* stream);
-size_t split_step_smem_bytes(int K, bool fp64_solve, int W);
+size_t split_step_smem_bytes(int K, bool fp64_solve, int W, bool adaptive);
 
 }  // namespace fib
 

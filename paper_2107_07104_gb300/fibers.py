@@ -24,6 +24,7 @@ _lock = threading.Lock()
 
 FIB_OK, FIB_EINVAL, FIB_ENOMEM, FIB_ECUDA, FIB_ENONFINITE, FIB_ETIMEOUT, FIB_ESTATE, FIB_ENOTSUP = range(8)
 FIB_MODE_FP32, FIB_MODE_FP64_THOMAS, FIB_MODE_SURROGATE = 0, 1, 2
+FIB_FLAG_ADAPTIVE = 1
 STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINITE", "FIB_ETIMEOUT",
                 "FIB_ESTATE", "FIB_ENOTSUP"]
 
@@ -33,7 +34,7 @@ EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_s
             "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
             "fibers_kernel_launches", "fibers_last_error", "fibers_destroy", "fibers_load_surrogate",
             "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward", "fibers_adam_step",
-            "fibers_feature_stats")
+            "fibers_feature_stats", "fibers_adaptive_stats")
 SUR_N_PARAMS = 17796
 SUR_BLOB_FLOATS = 3 + 5 + 5 + 4 + 4 + 5 + 5 + 5 + 5 + SUR_N_PARAMS
 SUR_WORK_PER_SAMPLE = 6 * 128 + 2 * 4
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
         L.fibers_read_state.argtypes = [vp, vp, sz, i32]
         L.fibers_write_state.argtypes = [vp, vp, sz, i32, i64]
         L.fibers_stats.argtypes = [vp, P(i64), P(i64)]
+        L.fibers_adaptive_stats.argtypes = [vp, P(i64)]
+        L.fibers_adaptive_stats.restype = ctypes.c_int
         L.fibers_synchronize.argtypes = [vp]
         L.fibers_get_tuning.argtypes = [vp, P(FibTuning)]
         L.fibers_set_tuning.argtypes = [vp, P(FibTuning)]
@@ -135,7 +138,7 @@ def make_params(p: dict, mode: int = FIB_MODE_FP32) -> FibParams:
         setattr(o, k, float(p[k]))
     o.stim_half_width = int(p.get("stim_half_width", 1))
     o.mode = int(p.get("mode", mode))
-    o.flags = 0
+    o.flags = int(p.get("flags", 0))
     o.reserved = 0
     return o
 
@@ -233,6 +236,12 @@ def fibers_stats(ctx):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().fibers_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
     return int(a.value), int(b.value)
+
+
+def fibers_adaptive_stats(ctx) -> int:
+    v = ctypes.c_int64()
+    _check(load().fibers_adaptive_stats(ctx, ctypes.byref(v)), ctx)
+    return int(v.value)
 
 
 def fibers_synchronize(ctx) -> None:
