@@ -30,7 +30,7 @@ class OrcParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("Cm", "gNa", "gK", "gL", "ENa", "EK", "EL", "Vrest", "sigma_eff", "Am", "h",
                  "dt_split", "dt_0d", "dt_1d", "stim_amplitude", "stim_duration")] + \
-               [("stim_half_width", ctypes.c_int32), ("splitting", ctypes.c_int32)]
+               [("stim_half_width", ctypes.c_int32), ("splitting", ctypes.c_int32), ("diffusion", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +64,8 @@ def lib():
             L.orc_cn_system.restype = ctypes.c_int
             L.orc_cn_step.argtypes = [P(OrcParams), ctypes.c_int, d, pd, pd]
             L.orc_cn_step.restype = ctypes.c_int
+            L.orc_ie_step.argtypes = [P(OrcParams), ctypes.c_int, d, pd, pd]
+            L.orc_ie_step.restype = ctypes.c_int
             L.orc_init_state.argtypes = [P(OrcParams), i64, P(ctypes.c_float), pd]
             L.orc_init_state.restype = ctypes.c_int
             L.orc_run_fibers.argtypes = [P(OrcParams), i32, P(i32), P(i32), P(i32), i32, P(i64), pd, pd,
@@ -80,6 +82,7 @@ def params(p: dict) -> OrcParams:
         setattr(o, k, float(p[k]))
     o.stim_half_width = int(p.get("stim_half_width", 1))
     o.splitting = int(p.get("splitting", 0))
+    o.diffusion = int(p.get("diffusion", 0))
     return o
 
 
@@ -149,6 +152,15 @@ def cn_step(p: dict, V, dt: float) -> np.ndarray:
     work = np.zeros(5 * n)
     if lib().orc_cn_step(ctypes.byref(params(p)), n, float(dt), _dp(V), _dp(work)):
         raise ValueError("CN step failed")
+    return V
+
+
+def ie_step(p: dict, V, dt: float) -> np.ndarray:
+    V = np.array(V, dtype=np.float64)
+    n = V.shape[0]
+    work = np.zeros(5 * n)
+    if lib().orc_ie_step(ctypes.byref(params(p)), n, float(dt), _dp(V), _dp(work)):
+        raise ValueError("implicit Euler step failed")
     return V
 
 

@@ -28,9 +28,14 @@
  *     (I - dt/2 M^-1 K) u+ = (I + dt/2 M^-1 K) u, solved by the Thomas
  *     algorithm (sec:improved_parallel_solver_for_fiber_based).
  *   * Heun's method eq:heun on the full state (V, m, h, n).
+ *   * Implicit Euler in the lumped form eq:lumping_implicit_euler_2:
+ *     (I - dt M^-1 K) u+ = u (selectable instead of CN).
  *   * Strang splitting eq:monodomain_strang: diffusion dt/2, reaction dt,
  *     diffusion dt/2, with the reaction sub-cycled in Heun steps of dt_0d and
- *     each diffusion half in CN steps of dt_1d.
+ *     each diffusion half in CN steps of dt_1d.  Selectable instead: Godunov
+ *     splitting eq:monodomain_godunov (diffusion dt, reaction dt), and the
+ *     orderings of the splitting figures (reaction dt/2, diffusion dt,
+ *     reaction dt/2; reaction dt, diffusion dt).
  *   * Stimulus (sec:stimulation_times_callbacks): current injection of
  *     stim_amplitude at the junction node and its neighbours (3 nodes),
  *     switched on for stim_duration after each firing time of the fiber's
@@ -55,7 +60,12 @@ typedef struct {
   double dt_split, dt_0d, dt_1d;
   double stim_amplitude, stim_duration;
   int32_t stim_half_width;
-  int32_t splitting; /* 0: Strang 1D/2-0D-1D/2 (only scheme the oracle runs) */
+  int32_t splitting; /* 0: Strang 1D(dt/2), 0D(dt), 1D(dt/2)   (eq:monodomain_strang, L1 = diffusion)
+                        1: Godunov 1D(dt), 0D(dt)              (eq:monodomain_godunov, L1 = diffusion)
+                        2: Strang 0D(dt/2), 1D(dt), 0D(dt/2)   (fig:strang_splitting)
+                        3: Godunov 0D(dt), 1D(dt)              (fig:godunov_splitting) */
+  int32_t diffusion; /* 0: Crank-Nicolson (eq:lumping_crank_nicolson_2)
+                        1: implicit Euler (eq:lumping_implicit_euler_2) */
 } orc_params;
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
@@ -177,6 +187,24 @@ static void cn_rows(int n, double r, const double* V, double* a, double* b, doub
   }
 }
 
+/* Rows of the lumped implicit-Euler system (eq:lumping_implicit_euler_2):
+ * (I - dt L) V+ = V with the same L as cn_rows: with q = c dt / h^2, interior
+ * rows (-q, 1 + 2q, -q), end rows (1 + 2q, -2q). */
+static void ie_rows(int n, double q, const double* V, double* a, double* b, double* cc, double* d) {
+  for (int i = 0; i < n; ++i) {
+    d[i] = V[i];
+    if (n == 1) {
+      a[i] = 0.0; b[i] = 1.0; cc[i] = 0.0;
+    } else if (i == 0) {
+      a[i] = 0.0; b[i] = 1.0 + 2.0 * q; cc[i] = -2.0 * q;
+    } else if (i == n - 1) {
+      a[i] = -2.0 * q; b[i] = 1.0 + 2.0 * q; cc[i] = 0.0;
+    } else {
+      a[i] = -q; b[i] = 1.0 + 2.0 * q; cc[i] = -q;
+    }
+  }
+}
+
 /* Diffusion prefactor c = sigma_eff / (Am Cm) (eq:monodomain). */
 static double diffusion_c(const orc_params* p) { return p->sigma_eff / (p->Am * p->Cm); }
 
@@ -186,6 +214,14 @@ int orc_cn_system(const orc_params* p, int n, double dt, const double* V, double
   if (n < 1) return ORC_EINVAL;
   cn_rows(n, diffusion_c(p) * dt / (p->h * p->h), V, a, b, c, d);
   return ORC_OK;
+}
+
+/* One implicit-Euler step of width dt on V (in place).  work: 5n doubles. */
+int orc_ie_step(const orc_params* p, int n, double dt, double* V, double* work) {
+  if (n < 1) return ORC_EINVAL;
+  double *a = work, *b = work + n, *c = work + 2 * n, *d = work + 3 * n, *w = work + 4 * n;
+  ie_rows(n, diffusion_c(p) * dt / (p->h * p->h), V, a, b, c, d);
+  return orc_thomas(n, a, b, c, d, V, w);
 }
 
 /* One CN step of width dt on V (in place).  work: 5n doubles. */
@@ -227,9 +263,13 @@ typedef struct {
 
 static int derive(const orc_params* p, orc_derived* o) {
   if (!(p->dt_split > 0.0) || !(p->dt_0d > 0.0) || !(p->dt_1d > 0.0) || !(p->h > 0.0) || !(p->Cm > 0.0) ||
-      !(p->Am > 0.0) || p->stim_half_width < 0 || p->splitting != 0)
+      !(p->Am > 0.0) || p->stim_half_width < 0 || p->splitting < 0 || p->splitting > 3 || p->diffusion < 0 ||
+      p->diffusion > 1)
     return ORC_EINVAL;
-  const double q0 = p->dt_split / p->dt_0d, q1 = 0.5 * p->dt_split / p->dt_1d;
+  /* Heun substeps per split step, and diffusion steps per diffusion phase:
+   * half a split step (Strang 1D-0D-1D) or a whole one (the others). */
+  const double q0 = p->dt_split / p->dt_0d;
+  const double q1 = (p->splitting == 0 ? 0.5 : 1.0) * p->dt_split / p->dt_1d;
   o->n_sub = (int64_t)nearbyint(q0);
   o->n_cn = (int64_t)nearbyint(q1);
   if (o->n_sub < 1 || o->n_cn < 1 || fabs(q0 - (double)o->n_sub) > 1e-9 * q0 ||
@@ -239,6 +279,7 @@ static int derive(const orc_params* p, orc_derived* o) {
   o->dt1 = p->dt_1d;
   o->P = substeps_of(p->stim_duration, p->dt_0d);
   o->EL = leak_reversal(p);
+  if (p->splitting == 2 && (o->n_sub % 2) != 0) return ORC_EINVAL; /* dt/2 in whole substeps */
   return ORC_OK;
 }
 
@@ -257,23 +298,40 @@ static int fiber_run(const orc_params* p, const orc_derived* o, int n, int junct
   int64_t row = 0;
   for (int64_t s = 0; s < n_steps; ++s) {
     const int64_t step = step0 + s;
-    /* 1D, first half: n_cn CN steps of dt_1d */
-    for (int64_t c = 0; c < o->n_cn; ++c)
-      if (orc_cn_step(p, n, o->dt1, V, work) != ORC_OK) return ORC_EINVAL;
-    /* 0D: n_sub Heun substeps at every node */
-    for (int64_t k = 0; k < o->n_sub; ++k) {
-      const int64_t kk = step * o->n_sub + k;
-      const int on = stim_on(fire_k, n_fire, o->P, kk);
-      for (int i = 0; i < n; ++i) {
-        double y[4] = {V[i], m[i], hh[i], nn[i]};
-        const double istim = (on && i >= lo && i <= hi) ? p->stim_amplitude : 0.0;
-        orc_heun_step(p, o->EL, y, istim, o->dt0);
-        V[i] = y[0]; m[i] = y[1]; hh[i] = y[2]; nn[i] = y[3];
-      }
+    /* reaction: Heun substeps k0 <= k < k1 of this split step at every node */
+#define ORC_REACT(k0, k1)                                                          \
+    for (int64_t k = (k0); k < (k1); ++k) {                                        \
+      const int64_t kk = step * o->n_sub + k;                                      \
+      const int on = stim_on(fire_k, n_fire, o->P, kk);                            \
+      for (int i = 0; i < n; ++i) {                                                \
+        double y[4] = {V[i], m[i], hh[i], nn[i]};                                  \
+        const double istim = (on && i >= lo && i <= hi) ? p->stim_amplitude : 0.0; \
+        orc_heun_step(p, o->EL, y, istim, o->dt0);                                 \
+        V[i] = y[0]; m[i] = y[1]; hh[i] = y[2]; nn[i] = y[3];                      \
+      }                                                                            \
     }
-    /* 1D, second half */
-    for (int64_t c = 0; c < o->n_cn; ++c)
-      if (orc_cn_step(p, n, o->dt1, V, work) != ORC_OK) return ORC_EINVAL;
+    /* diffusion: n_cn steps of dt_1d with the selected method */
+#define ORC_DIFFUSE()                                                                          \
+    for (int64_t c = 0; c < o->n_cn; ++c)                                                      \
+      if ((p->diffusion == 1 ? orc_ie_step(p, n, o->dt1, V, work)                              \
+                             : orc_cn_step(p, n, o->dt1, V, work)) != ORC_OK) return ORC_EINVAL;
+    if (p->splitting == 0) {        /* 1D(dt/2), 0D(dt), 1D(dt/2) */
+      ORC_DIFFUSE()
+      ORC_REACT(0, o->n_sub)
+      ORC_DIFFUSE()
+    } else if (p->splitting == 1) { /* 1D(dt), 0D(dt) */
+      ORC_DIFFUSE()
+      ORC_REACT(0, o->n_sub)
+    } else if (p->splitting == 2) { /* 0D(dt/2), 1D(dt), 0D(dt/2) */
+      ORC_REACT(0, o->n_sub / 2)
+      ORC_DIFFUSE()
+      ORC_REACT(o->n_sub / 2, o->n_sub)
+    } else {                        /* 0D(dt), 1D(dt) */
+      ORC_REACT(0, o->n_sub)
+      ORC_DIFFUSE()
+    }
+#undef ORC_DIFFUSE
+#undef ORC_REACT
     if (samples && sample_every > 0 && ((s + 1) % sample_every) == 0) {
       memcpy(samples + row * sample_stride, V, sizeof(double) * (size_t)n);
       ++row;

@@ -171,6 +171,47 @@ def test_cn_cosine_mode_closed_form(k):
     assert np.max(np.abs(x - g * v)) <= 1e-12
 
 
+@pytest.mark.parametrize("k", [1, 3, 9])
+def test_implicit_euler_cosine_mode_closed_form(k):
+    """Same eigenvector as above: m implicit-Euler steps (eq:lumping_implicit_euler_2)
+    scale it by (1 / (1 - lambda dt))^m -- a different factor from CN's, so the
+    two methods cannot be confused."""
+    p = P()
+    n, dt, m = 50, 3e-3, 30
+    c = p["sigma_eff"] / (p["Am"] * p["Cm"])
+    i = np.arange(n)
+    v = np.cos(k * np.pi * i / (n - 1))
+    lam = -(4 * c / p["h"] ** 2) * np.sin(k * np.pi / (2 * (n - 1))) ** 2
+    g = (1.0 / (1.0 - lam * dt)) ** m
+    x = v.copy()
+    for _ in range(m):
+        x = oracle.ie_step(p, x, dt)
+    assert np.max(np.abs(x - g * v)) <= 1e-12
+    g_cn = ((1 + lam * dt / 2) / (1 - lam * dt / 2)) ** m
+    assert abs(g - g_cn) > 1e-6  # far above the 1e-12 check
+
+
+def test_implicit_euler_matches_dense_solve_and_conserves_weighted_sum():
+    # (I - dt M_L^-1 K) u+ = u assembled densely from the FEM matrices
+    p = P()
+    rng = np.random.default_rng(11)
+    c = p["sigma_eff"] / (p["Am"] * p["Cm"])
+    for n in (2, 3, 40):
+        h = p["h"]
+        Kst = np.zeros((n, n))
+        for e in range(n - 1):
+            Kst[e:e + 2, e:e + 2] += -(1.0 / h) * np.array([[1.0, -1.0], [-1.0, 1.0]])
+        Mlump = np.full(n, h)
+        Mlump[0] = Mlump[-1] = h / 2
+        A = np.eye(n) - 1.7e-3 * c * (Kst / Mlump[:, None])
+        V = rng.normal(size=n) * 15 - 60
+        x = oracle.ie_step(p, V, 1.7e-3)
+        assert np.max(np.abs(x - np.linalg.solve(A, V))) <= 1e-11
+        w = np.ones(n)
+        w[0] = w[-1] = 0.5
+        assert abs(w @ x - w @ V) <= 1e-12 * abs(w @ V)
+
+
 def test_cn_conserves_lumped_mass_weighted_sum():
     p = P()
     rng = np.random.default_rng(7)
@@ -203,10 +244,15 @@ def _charge_run(n, junction, fire, n_steps, **kw):
     return p, w @ (st[:n] - V0)
 
 
-def test_stimulus_charge_balance_centre():
-    # Heun is exact for a constant RHS and CN conserves the weighted sum, so
-    # the weighted sum grows by A/Cm per on-substep at each of the 3 nodes.
-    p, q = _charge_run(101, 50, [0.0], 40)
+@pytest.mark.parametrize("splitting,diffusion", [(0, 0), (1, 1), (2, 0), (3, 1), (2, 1)])
+def test_stimulus_charge_balance_centre(splitting, diffusion):
+    # Heun is exact for a constant RHS and both diffusion methods conserve the
+    # weighted sum, so the weighted sum grows by A/Cm per on-substep at each
+    # of the 3 nodes, whatever the splitting's ordering.
+    kw = dict(splitting=splitting, diffusion=diffusion)
+    if splitting == 2:
+        kw.update(dt_0d=7.5e-4, stim_duration=0.075)  # whole half steps; 100 substeps
+    p, q = _charge_run(101, 50, [0.0], 40, **kw)
     P_sub = round(p["stim_duration"] / p["dt_0d"])
     assert P_sub == 100
     expect = 3 * P_sub * p["dt_0d"] * p["stim_amplitude"] / p["Cm"]
@@ -287,6 +333,74 @@ def test_strang_heun_cn_is_second_order_on_a_fiber():
     errs = [np.max(np.abs(finals[dt][:n] - ref[:n])) for dt in dts]
     orders = _observed_orders(errs)
     assert np.all((orders > 1.8) & (orders < 2.2)), (errs, orders)
+
+
+@pytest.mark.parametrize("splitting", [1, 3])
+def test_godunov_implicit_euler_is_first_order_on_a_fiber(splitting):
+    # eq:monodomain_godunov with implicit Euler: both the splitting and the
+    # diffusion method are first order, in either ordering
+    n = 101
+    x = np.arange(n) * 0.01
+    t_end = 0.96
+    dts = (0.012, 0.006, 0.003)
+    ref_dt = 0.012 / 64
+    finals = {}
+    for dt in dts + (ref_dt,):
+        p = P(dt_split=dt, dt_0d=dt / 3, dt_1d=dt, splitting=splitting, diffusion=1)
+        vm0 = (p["Vrest"] + 30.0 * np.exp(-((x - 0.5) / 0.1) ** 2)).astype(np.float32)
+        st = oracle.init_state(p, n, vm0)
+        oracle.run(p, [n], [0], [50], [0, 0], [], st, 0, int(round(t_end / dt)), n_threads=1)
+        finals[dt] = st.copy()
+    errs = [np.max(np.abs(finals[dt][:n] - finals[ref_dt][:n])) for dt in dts]
+    orders = _observed_orders(errs)
+    assert np.all((orders > 0.85) & (orders < 1.2)), (errs, orders)
+
+
+def test_strang_0d_1d_0d_is_second_order_and_agrees_with_1d_0d_1d():
+    # the figure's ordering of eq:monodomain_strang is second order too, and
+    # both orderings converge to the same solution
+    n = 101
+    x = np.arange(n) * 0.01
+    t_end = 0.96
+    dts = (0.012, 0.006, 0.003)
+    ref_dt = 0.012 / 32
+    finals = {}
+    for splitting in (0, 2):
+        for dt in dts + (ref_dt,):
+            p = P(dt_split=dt, dt_0d=dt / 4, dt_1d=dt / 2 if splitting == 0 else dt, splitting=splitting)
+            vm0 = (p["Vrest"] + 30.0 * np.exp(-((x - 0.5) / 0.1) ** 2)).astype(np.float32)
+            st = oracle.init_state(p, n, vm0)
+            oracle.run(p, [n], [0], [50], [0, 0], [], st, 0, int(round(t_end / dt)), n_threads=1)
+            finals[splitting, dt] = st.copy()
+        errs = [np.max(np.abs(finals[splitting, dt][:n] - finals[splitting, ref_dt][:n])) for dt in dts]
+        orders = _observed_orders(errs)
+        assert np.all((orders > 1.8) & (orders < 2.2)), (splitting, errs, orders)
+    # the two orderings differ at a coarse step but not at the reference step
+    coarse = np.max(np.abs(finals[0, dts[0]][:n] - finals[2, dts[0]][:n]))
+    fine = np.max(np.abs(finals[0, ref_dt][:n] - finals[2, ref_dt][:n]))
+    assert coarse > 1e-4 and fine < coarse / 100, (coarse, fine)
+
+
+@pytest.mark.parametrize("splitting", [0, 1, 2, 3])
+def test_single_node_fiber_is_plain_heun_in_every_splitting(splitting):
+    # no diffusion on one node: every ordering reduces to n_sub Heun substeps
+    p = P(splitting=splitting, dt_0d=7.5e-4, diffusion=splitting % 2)
+    st = oracle.init_state(p, 1, np.array([p["Vrest"] + 12.0], np.float32))
+    oracle.run(p, [1], [0], [0], [0, 0], [], st, 0, 50, n_threads=1)
+    y = np.array([p["Vrest"] + 12.0, *oracle.gates_inf(p, p["Vrest"])])
+    y[0] = float(np.float32(y[0]))
+    for _ in range(50 * 4):
+        y = oracle.heun_step(p, y, 7.5e-4)
+    assert np.array_equal(st, y)
+
+
+def test_invalid_schemes_are_rejected():
+    st = oracle.init_state(P(), 10, None)
+    with pytest.raises(ValueError):  # 0D-1D-0D needs an even substep count
+        oracle.run(P(splitting=2), [10], [0], [5], [0, 0], [], st, 0, 1, n_threads=1)
+    for bad in (dict(splitting=4), dict(diffusion=2), dict(splitting=-1)):
+        with pytest.raises(ValueError):
+            oracle.run(P(**bad), [10], [0], [5], [0, 0], [], st, 0, 1, n_threads=1)
 
 
 # --------------------------------------------------------------------------
