@@ -340,6 +340,7 @@ def run_gpu(args, world, rank, local, dist):
     clocks = clk.summary()
     sur = None if args.no_surrogate else surrogate_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     adaptive = None if args.no_adaptive else adaptive_leg(args, w, tune, stream, dev, total, per_gpu_rate)
+    schemes = None if args.no_schemes else schemes_leg(args, w, tune, stream, dev, total)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
@@ -369,6 +370,7 @@ def run_gpu(args, world, rank, local, dist):
         "finite": finite,
         "surrogate": sur,
         "adaptive": adaptive,
+        "schemes": schemes,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -471,6 +473,51 @@ def adaptive_leg(args, w, tune, stream, dev, total, plain_rate):
             "max_abs_mv_vs_plain_fp32_at_end": float(np.max(np.abs(va - vp)))}
 
 
+# Scheme variants timed on the same bundle: (name, parameter overrides).  The
+# two thesis configurations compare a first-order scheme at a small step with
+# a second-order one at a large step; their accuracy against a fine reference
+# is measured by the oracle tests, their cost here.
+SCHEME_LEGS = [
+    ("strang 1D-0D-1D, CN, dt 3e-3 (default)", {}),
+    ("strang 0D-1D-0D, CN, dt 4e-3, dt_0D 2e-3, dt_1D 4e-3",
+     dict(splitting=2, diffusion=0, dt_split=4e-3, dt_0d=2e-3, dt_1d=4e-3)),
+    ("godunov 0D-1D, IE, dt 5e-4, dt_0D 1e-4, dt_1D 5e-4",
+     dict(splitting=3, diffusion=1, dt_split=5e-4, dt_0d=1e-4, dt_1d=5e-4)),
+    ("strang 0D-1D-0D, IE, dt 3e-3, dt_0D 5e-4, dt_1D 1.5e-3",
+     dict(splitting=2, diffusion=1, dt_0d=5e-4, dt_1d=1.5e-3)),
+]
+
+
+def schemes_leg(args, w, tune, stream, dev, total, sim_ms=3.0):
+    """Each scheme variant on the bundle over the same simulated interval:
+    node-updates/s per split step and simulated milliseconds per second."""
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+    out = {}
+    for name, over in SCHEME_LEGS:
+        ws = w.with_steps(w.n_steps)
+        ws.params = dict(w.params)
+        ws.params.update(over)
+        dt = ws.params["dt_split"]
+        steps = int(round(sim_ms / dt))
+        warm = max(3, steps // 10)
+        with F.Fibers.from_workload(ws, tuning=tune, stream=stream) as fib:
+            fib.step(warm)
+            fib.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            fib.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            finite = bool(np.all(np.isfinite(fib.read_vm())))
+        out[name] = {"node_updates_per_s": float(total) * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                     "simulated_ms_per_s": steps * dt / (ms / 1e3), "steps": steps, "finite": finite}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,6 +536,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true")
+    ap.add_argument("--no-schemes", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -75,12 +75,34 @@ enum {
   FIB_FLAG_ADAPTIVE = 1
 };
 
+/* Operator-splitting orderings (fib_params.splitting).  The splitting
+ * equations name the diffusion operator L1, so they read diffusion first;
+ * the splitting figures order the substeps reaction first.  Both are offered.
+ * Reaction phases are whole Heun substeps of dt_0d, diffusion phases whole
+ * steps of dt_1d. */
+enum {
+  FIB_SPLIT_STRANG_1D0D1D = 0,  /* diffusion dt/2, reaction dt, diffusion dt/2 (eq:monodomain_strang) */
+  FIB_SPLIT_GODUNOV_1D0D = 1,   /* diffusion dt, reaction dt (eq:monodomain_godunov) */
+  FIB_SPLIT_STRANG_0D1D0D = 2,  /* reaction dt/2, diffusion dt, reaction dt/2 (fig:strang_splitting);
+                                   dt_split / dt_0d must be even */
+  FIB_SPLIT_GODUNOV_0D1D = 3    /* reaction dt, diffusion dt (fig:godunov_splitting) */
+};
+
+/* Diffusion time-stepping method (fib_params.diffusion). */
+enum {
+  FIB_DIFFUSION_CRANK_NICOLSON = 0,  /* (I - dt/2 M^-1 K) u+ = (I + dt/2 M^-1 K) u (eq:lumping_crank_nicolson_2) */
+  FIB_DIFFUSION_IMPLICIT_EULER = 1   /* (I - dt M^-1 K) u+ = u (eq:lumping_implicit_euler_2) */
+};
+
 /* Model and discretisation parameters (sec:subcelullar_model, eq:monodomain,
  * eq:monodomain_strang).  ENa, EK and EL are absolute reversal potentials;
  * EL = NaN asks the library to derive it so that (Vrest, m_inf, h_inf, n_inf)
  * is an exact rest state.  The HH rates are those of Hodgkin & Huxley 1952 in
- * the depolarisation u = V - Vrest.  dt_split / dt_0d and (dt_split/2) /
- * dt_1d must be whole numbers.  A firing at time t_f switches the stimulus
+ * the depolarisation u = V - Vrest.  dt_split / dt_0d must be a whole number,
+ * and so must the diffusion phase's length over dt_1d: (dt_split/2) / dt_1d
+ * for FIB_SPLIT_STRANG_1D0D1D, dt_split / dt_1d for the other orderings.
+ * FIB_MODE_SURROGATE takes only the default ordering and Crank-Nicolson.
+ * A firing at time t_f switches the stimulus
  * on for Heun substeps k with k_f <= k < k_f + P, k_f = round(t_f / dt_0d)
  * (half to even), P = round(stim_duration / dt_0d), at junction nodes
  * j - stim_half_width .. j + stim_half_width (clipped to the fiber).  */
@@ -91,8 +113,10 @@ typedef struct {
   double stim_amplitude, stim_duration;
   int32_t stim_half_width;
   int32_t mode;     /* FIB_MODE_* */
-  int32_t flags;    /* FIB_FLAG_* bits (0: none) */
-  int32_t reserved; /* must be 0 */
+  int32_t flags;     /* FIB_FLAG_* bits (0: none) */
+  int32_t splitting; /* FIB_SPLIT_* (0: Strang, diffusion first) */
+  int32_t diffusion; /* FIB_DIFFUSION_* (0: Crank-Nicolson) */
+  int32_t reserved;  /* must be 0 */
 } fib_params;
 
 /* Launch shape.  Zero fields mean "choose automatically". */

@@ -127,6 +127,12 @@ void rest_gates(double u, double* m, double* h, double* n) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+// Length of one diffusion phase: half a split step for Strang 1D-0D-1D, a
+// whole one for the other orderings.
+double diffusion_phase(const fib_params* p) {
+  return (p->splitting == FIB_SPLIT_STRANG_1D0D1D ? 0.5 : 1.0) * p->dt_split;
+}
+
 fib_status validate(const fib_params* p) {
   if (!p) return fail(nullptr, FIB_EINVAL, "params is NULL");
   const double vals[] = {p->Cm, p->Am, p->h, p->dt_split, p->dt_0d, p->dt_1d, p->sigma_eff};
@@ -148,11 +154,20 @@ fib_status validate(const fib_params* p) {
     return fail(nullptr, FIB_EINVAL, "unknown flags or nonzero reserved field");
   if ((p->flags & FIB_FLAG_ADAPTIVE) && p->mode == FIB_MODE_SURROGATE)
     return fail(nullptr, FIB_EINVAL, "adaptive computation is not available in surrogate mode");
-  const double q0 = p->dt_split / p->dt_0d, q1 = 0.5 * p->dt_split / p->dt_1d;
+  if (p->splitting < FIB_SPLIT_STRANG_1D0D1D || p->splitting > FIB_SPLIT_GODUNOV_0D1D)
+    return fail(nullptr, FIB_EINVAL, "unknown splitting %d", p->splitting);
+  if (p->diffusion != FIB_DIFFUSION_CRANK_NICOLSON && p->diffusion != FIB_DIFFUSION_IMPLICIT_EULER)
+    return fail(nullptr, FIB_EINVAL, "unknown diffusion method %d", p->diffusion);
+  if (p->mode == FIB_MODE_SURROGATE &&
+      (p->splitting != FIB_SPLIT_STRANG_1D0D1D || p->diffusion != FIB_DIFFUSION_CRANK_NICOLSON))
+    return fail(nullptr, FIB_EINVAL, "surrogate mode runs only Strang 1D-0D-1D with Crank-Nicolson");
+  const double q0 = p->dt_split / p->dt_0d, q1 = diffusion_phase(p) / p->dt_1d;
   const double r0 = std::nearbyint(q0), r1 = std::nearbyint(q1);
   if (r0 < 1 || r1 < 1 || std::fabs(q0 - r0) > 1e-9 * q0 || std::fabs(q1 - r1) > 1e-9 * q1)
-    return fail(nullptr, FIB_EINVAL, "dt_split/dt_0d and dt_split/(2 dt_1d) must be whole numbers >= 1");
+    return fail(nullptr, FIB_EINVAL, "dt_split/dt_0d and the diffusion phase over dt_1d must be whole numbers >= 1");
   if (r0 > 1000 || r1 > 1000) return fail(nullptr, FIB_EINVAL, "too many substeps per split step");
+  if (p->splitting == FIB_SPLIT_STRANG_0D1D0D && ((int64_t)r0 % 2) != 0)
+    return fail(nullptr, FIB_EINVAL, "0D-1D-0D Strang needs an even number of Heun substeps per split step");
   return FIB_OK;
 }
 
@@ -382,6 +397,13 @@ StepArgs make_args(fib_ctx* c) {
   a.r = c->r;
   a.n_sub = (int32_t)c->n_sub;
   a.n_cn = (int32_t)c->n_cn;
+  switch (c->p.splitting) {
+    case FIB_SPLIT_STRANG_1D0D1D: a.k_split = 0; a.n_cn2 = a.n_cn; break;
+    case FIB_SPLIT_GODUNOV_1D0D: a.k_split = 0; a.n_cn2 = 0; break;
+    case FIB_SPLIT_STRANG_0D1D0D: a.k_split = a.n_sub / 2; a.n_cn2 = 0; break;
+    default: a.k_split = a.n_sub; a.n_cn2 = 0; break;  // FIB_SPLIT_GODUNOV_0D1D
+  }
+  a.implicit_euler = c->p.diffusion == FIB_DIFFUSION_IMPLICIT_EULER ? 1 : 0;
   a.pulse = (int32_t)c->pulse;
   a.hw = c->p.stim_half_width;
   a.n_mu = c->n_mu;
@@ -602,10 +624,13 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
 
   // derived constants
   c->n_sub = (int64_t)std::nearbyint(p->dt_split / p->dt_0d);
-  c->n_cn = (int64_t)std::nearbyint(0.5 * p->dt_split / p->dt_1d);
+  c->n_cn = (int64_t)std::nearbyint(diffusion_phase(p) / p->dt_1d);
   c->pulse = (int64_t)std::nearbyint(p->stim_duration / p->dt_0d);
   const double cdiff = p->sigma_eff / (p->Am * p->Cm);
-  c->r = cdiff * p->dt_1d / (p->h * p->h);
+  // The tables hold (I - r/2 L') with L' the unit-spaced [1 -2 1] stencil:
+  // r = c dt_1d / h^2 gives the CN left-hand side, twice that the implicit
+  // Euler one.
+  c->r = (p->diffusion == FIB_DIFFUSION_IMPLICIT_EULER ? 2.0 : 1.0) * cdiff * p->dt_1d / (p->h * p->h);
   rest_gates(0.0, &c->m0, &c->h0, &c->n0);
   if (std::isnan(p->EL)) {
     const double ina = p->gNa * c->m0 * c->m0 * c->m0 * c->h0 * (p->Vrest - p->ENa);

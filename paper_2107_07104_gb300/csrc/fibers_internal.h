@@ -65,11 +65,16 @@ struct StepArgs {
   const int64_t* step_base;  // device-resident index of the next split step
   int32_t* flag;           // bit 0: non-finite state seen
   HHConst hh;
-  double r;                // c dt_1d / h^2
+  double r;                // tridiagonal-table parameter: c dt_1d / h^2 (CN), 2 c dt_1d / h^2 (IE)
   int64_t step_offset;     // this launch starts at *step_base + step_offset
   int32_t n_steps;         // split steps in this launch
   int32_t n_sub;           // Heun substeps per split step
-  int32_t n_cn;            // CN steps per diffusion half
+  // One split step runs: reaction substeps [0, k_split), n_cn diffusion
+  // steps, reaction substeps [k_split, n_sub), n_cn2 diffusion steps.
+  int32_t k_split;
+  int32_t n_cn;            // diffusion steps of the first diffusion phase
+  int32_t n_cn2;           // diffusion steps of the second diffusion phase
+  int32_t implicit_euler;  // 1: right-hand side u (eq:lumping_implicit_euler_2); 0: CN
   int32_t pulse;           // stimulus length in substeps
   int32_t hw;              // stimulus half width (nodes)
   int32_t n_mu;
@@ -78,7 +83,7 @@ struct StepArgs {
   int32_t W;               // warps per CTA
   int32_t packed;          // 1: reaction step on node pairs with FP32x2 arithmetic
   int32_t lean;            // 1: kernel built for 3 CTAs of 256 threads per SM (<= 85 registers)
-  int32_t phases;          // bit 0: first CN half, bit 1: reaction, bit 2: second CN half
+  int32_t phases;          // bit 0: first diffusion phase, bit 1: reaction, bit 2: second diffusion phase
   // adaptive computation: skip fibers in equilibrium with no pulse due
   uint8_t* quiet;          // per fiber: 1 = passed the equilibrium test at the end of its last launch
   unsigned long long* skipped;  // fiber-steps skipped

@@ -54,6 +54,8 @@ DEFAULT_PARAMS = dict(
     stim_amplitude=1200.0,  # uA/cm^2
     stim_duration=0.1,     # ms
     stim_half_width=1,     # nodes j-1..j+1
+    splitting=0,           # Strang, diffusion dt/2 - reaction dt - diffusion dt/2
+    diffusion=0,           # Crank-Nicolson
 )
 
 

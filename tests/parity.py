@@ -8,6 +8,7 @@ import numpy as np
 
 import oracle
 from paper_2107_07104_gb300 import fibers as F
+from paper_2107_07104_gb300 import workloads as W
 
 # Tolerances for the FP32 path against the FP64 oracle over a trajectory.
 MAX_ABS_MV = 0.5
@@ -71,3 +72,25 @@ def activation_times(samples: np.ndarray, dt: float, threshold: float = 0.0) -> 
     v1 = s[kk + 1, idx]
     t[idx] = (kk + 1 + (threshold - v0) / (v1 - v0)) * dt
     return t
+
+
+EDGE_LENGTHS = [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 16, 17, 31, 32, 33, 47, 48, 49, 63, 64, 65, 127, 128, 129,
+                255, 256, 257, 383, 384, 385, 511, 512, 513, 700]
+
+
+def edge_workload(n_steps, seed=11, amp=None):
+    """Fibers of 1..700 nodes: chunk-aligned and ragged tails, 1-3 node
+    fibers, junctions at both ends, never-stimulated fibers, noisy start."""
+    rng = np.random.default_rng(seed)
+    lens = np.array(EDGE_LENGTHS, np.int32)
+    n = lens.shape[0]
+    w = W.small_ragged(seed, n, 1, 2, n_steps)
+    w.n_nodes = lens
+    w.junction = W.centre_junctions(rng, lens, 0.05)
+    w.junction[3] = 0          # junction at the first node
+    w.junction[10] = lens[10] - 1  # and at the last
+    w.mu_of_fiber = rng.integers(-1, w.n_mu, size=n).astype(np.int32)  # -1: never stimulated
+    w.vm0 = (w.params["Vrest"] + rng.normal(0, 0.5, size=int(lens.sum()))).astype(np.float32)
+    if amp is not None:
+        w.params["stim_amplitude"] = amp
+    return w

@@ -66,6 +66,12 @@ def _create(**over):
     (dict(n_nodes=[5, 0, 7]), "nodes"),
     (dict(junction_node=[0, 9, 1]), "junction"),
     (dict(mu_of_fiber=[0, -2, 1]), "motor unit"),
+    (dict(splitting=4), "unknown splitting"),
+    (dict(diffusion=2), "unknown diffusion"),
+    (dict(splitting=2), "even number"),                    # 3 Heun substeps cannot be halved
+    (dict(splitting=1, dt_1d=0.002), "whole numbers"),     # Godunov diffuses over the whole dt_split
+    (dict(splitting=3, mode=F.FIB_MODE_SURROGATE), "surrogate mode runs only"),
+    (dict(diffusion=1, mode=F.FIB_MODE_SURROGATE), "surrogate mode runs only"),
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, over, text):
     with pytest.raises(F.FibersError) as ei:

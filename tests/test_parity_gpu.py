@@ -10,7 +10,7 @@ import oracle
 from paper_2107_07104_gb300 import fibers as F
 from paper_2107_07104_gb300 import workloads as W
 
-from parity import (ACT_TIME_MS, MAX_ABS_MV, REL_L2, activation_times, errors, gpu_checkpoints,
+from parity import (ACT_TIME_MS, MAX_ABS_MV, REL_L2, activation_times, edge_workload, errors, gpu_checkpoints,
                     oracle_checkpoints, select_fibers)
 
 pytestmark = pytest.mark.gpu
@@ -45,24 +45,8 @@ def test_single_fiber_full_trajectory():
     assert dt_act <= ACT_TIME_MS
 
 
-EDGE_LENGTHS = [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 16, 17, 31, 32, 33, 47, 48, 49, 63, 64, 65, 127, 128, 129,
-                255, 256, 257, 383, 384, 385, 511, 512, 513, 700]
-
-
 def _edge_workload(n_steps, seed=11, amp=None):
-    rng = np.random.default_rng(seed)
-    lens = np.array(EDGE_LENGTHS, np.int32)
-    n = lens.shape[0]
-    w = W.small_ragged(seed, n, 1, 2, n_steps)
-    w.n_nodes = lens
-    w.junction = W.centre_junctions(rng, lens, 0.05)
-    w.junction[3] = 0          # junction at the first node
-    w.junction[10] = lens[10] - 1  # and at the last
-    w.mu_of_fiber = rng.integers(-1, w.n_mu, size=n).astype(np.int32)  # -1: never stimulated
-    w.vm0 = (w.params["Vrest"] + rng.normal(0, 0.5, size=int(lens.sum()))).astype(np.float32)
-    if amp is not None:
-        w.params["stim_amplitude"] = amp
-    return w
+    return edge_workload(n_steps, seed, amp)
 
 
 @pytest.mark.parametrize("K,Wc", [(4, 0), (8, 0), (8, 8), (12, 0), (16, 0), (16, 2)])
