@@ -51,6 +51,7 @@ struct HHConst {  // Hodgkin-Huxley constants in the depolarisation u = V - Vres
   float gNa_uNa, gK_uK, gL_uL;  // products of the above, rounded once from FP64
 };
 
+
 struct StepArgs {
   float* u;  // SoA state in the padded layout; u = V - Vrest
   float* m;

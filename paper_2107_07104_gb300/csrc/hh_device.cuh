@@ -36,14 +36,14 @@ constexpr float kE10 = 2.718281828459045f;   // e^1
 // e^z - 1) and is 0/0 at the point itself.  Within |z_m| < 0.01 (|z_n'| <
 // 0.001) the Bernoulli series z/(e^z - 1) = 1 - z/2 + z^2/12 - ... replaces
 // it (remainder below 2e-11 relative; the direct form's error at the edge of
-// that window is about 3e-5 relative and shrinks as 1/|z| outside it).  A
-// node only sits in those 0.1 mV windows for a substep or two per action
-// potential; the paired form evaluates the series behind a warp vote.
+// that window is about 3e-5 relative and shrinks as 1/|z| outside it).  Both
+// forms choose per node with a branch-free select.
 //
 // Signs: the code carries nz = -z, -alpha_m, -alpha_n, -beta_h, -(dm/dt) and
 // -(dn/dt), so that every subtraction becomes an FMA with a constant of the
-// right sign and the packed FP32x2 form (which has no negate modifier) needs
-// no extra instruction.  Both forms execute the same operations.
+// right sign or a plain subtraction, and the packed FP32x2 form (which has no
+// negate modifier) needs no extra instruction.  Both forms execute the same
+// operations.
 __device__ __forceinline__ bool near_singular(float nzm, float nzn) {
   return fabsf(nzm) < 0.01f || fabsf(nzn) < 0.001f;
 }
@@ -75,15 +75,15 @@ __device__ __forceinline__ Deriv hh_rhs(float u, float m, float h, float n, floa
   const float bn = ex2_approx(fmaf(u, -kLog2e / 80.0f, -3.0f));                   // 0.125 e^(-u/80)
   const float nzm = fmaf(u, 0.1f, -2.5f);    // -(25 - u) / 10
   const float nzn = fmaf(u, 0.01f, -0.1f);   // -(10 - u) / 100
-  // branch-free here (a branch would split the unrolled node loop into
-  // blocks the scheduler cannot interleave); the packed form votes instead
+  // branch-free (a branch would split the unrolled node loop into blocks
+  // the scheduler cannot interleave)
   const float nam = fabsf(nzm) < 0.01f ? nam_series(nzm) : nzm * rcp_approx(fmaf(kE25, E, -1.0f));
   const float nan_ = fabsf(nzn) < 0.001f ? nan_series(nzn) : nzn * rcp_approx(fmaf(kE10, E, -1.0f));
   const float nbh = rcp_approx(fmaf(-kE30, E, -1.0f));
   Deriv d;
-  d.m = fmaf(fmaf(nam, -1.0f, bm), m, nam);     // (am + bm) m - am
-  d.h = fmaf(fmaf(ah, -1.0f, nbh), h, ah);      // ah - (ah + bh) h
-  d.n = fmaf(fmaf(nan_, -1.0f, bn), n, nan_);   // (an + bn) n - an
+  d.m = fmaf(bm - nam, m, nam);     // (am + bm) m - am
+  d.h = fmaf(nbh - ah, h, ah);      // ah - (ah + bh) h
+  d.n = fmaf(bn - nan_, n, nan_);   // (an + bn) n - an
   const float A = (m * m) * (m * h);
   float B = n * n;
   B = B * B;
@@ -108,11 +108,17 @@ __device__ __forceinline__ void heun_nodes(float (&u)[K], float (&m)[K], float (
     const float m1 = fmaf(-dt, f0.m, m[j]);
     const float h1 = fmaf(dt, f0.h, h[j]);
     const float n1 = fmaf(-dt, f0.n, n[j]);
+    // y + dt/2 (f0 + f1) as (y + dt/2 f0) + dt/2 f1: y is then dead once
+    // the predictor is formed
+    u[j] = fmaf(hdt, f0.u, u[j]);
+    m[j] = fmaf(-hdt, f0.m, m[j]);
+    h[j] = fmaf(hdt, f0.h, h[j]);
+    n[j] = fmaf(-hdt, f0.n, n[j]);
     const Deriv f1 = hh_rhs(u1, m1, h1, n1, s, c);
-    u[j] = fmaf(hdt, f0.u + f1.u, u[j]);
-    m[j] = fmaf(-hdt, f0.m + f1.m, m[j]);
-    h[j] = fmaf(hdt, f0.h + f1.h, h[j]);
-    n[j] = fmaf(-hdt, f0.n + f1.n, n[j]);
+    u[j] = fmaf(hdt, f1.u, u[j]);
+    m[j] = fmaf(-hdt, f1.m, m[j]);
+    h[j] = fmaf(hdt, f1.h, h[j]);
+    n[j] = fmaf(-hdt, f1.n, n[j]);
   }
 }
 
