@@ -30,7 +30,8 @@ class OrcParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("Cm", "gNa", "gK", "gL", "ENa", "EK", "EL", "Vrest", "sigma_eff", "Am", "h",
                  "dt_split", "dt_0d", "dt_1d", "stim_amplitude", "stim_duration")] + \
-               [("stim_half_width", ctypes.c_int32), ("splitting", ctypes.c_int32), ("diffusion", ctypes.c_int32)]
+               [("stim_half_width", ctypes.c_int32), ("splitting", ctypes.c_int32), ("diffusion", ctypes.c_int32),
+                ("exp_approx", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +54,8 @@ def lib():
             d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
             pd = P(d)
             L.orc_hh_rates.argtypes = [P(OrcParams), d, pd]
+            L.orc_exp_star.argtypes = [d]
+            L.orc_exp_star.restype = d
             L.orc_gates_inf.argtypes = [P(OrcParams), d, pd]
             L.orc_leak_reversal_exact.argtypes = [P(OrcParams)]
             L.orc_leak_reversal_exact.restype = d
@@ -83,6 +86,7 @@ def params(p: dict) -> OrcParams:
     o.stim_half_width = int(p.get("stim_half_width", 1))
     o.splitting = int(p.get("splitting", 0))
     o.diffusion = int(p.get("diffusion", 0))
+    o.exp_approx = int(p.get("exp_approx", 0))
     return o
 
 
@@ -98,6 +102,10 @@ def hh_rates(p: dict, V: float) -> np.ndarray:
     out = np.zeros(6)
     lib().orc_hh_rates(ctypes.byref(params(p)), float(V), _dp(out))
     return out
+
+
+def exp_star(x: float) -> float:
+    return float(lib().orc_exp_star(float(x)))
 
 
 def gates_inf(p: dict, V: float) -> np.ndarray:

@@ -28,6 +28,8 @@
  *     (I - dt/2 M^-1 K) u+ = (I + dt/2 M^-1 K) u, solved by the Thomas
  *     algorithm (sec:improved_parallel_solver_for_fiber_based).
  *   * Heun's method eq:heun on the full state (V, m, h, n).
+ *   * Optionally the thesis's approximated exponential exp*(x) =
+ *     (1 + x/1024)^1024 (eq:apx-e-function) in place of every exp of the rates.
  *   * Implicit Euler in the lumped form eq:lumping_implicit_euler_2:
  *     (I - dt M^-1 K) u+ = u (selectable instead of CN).
  *   * Strang splitting eq:monodomain_strang: diffusion dt/2, reaction dt,
@@ -66,6 +68,8 @@ typedef struct {
                         3: Godunov 0D(dt), 1D(dt)              (fig:godunov_splitting) */
   int32_t diffusion; /* 0: Crank-Nicolson (eq:lumping_crank_nicolson_2)
                         1: implicit Euler (eq:lumping_implicit_euler_2) */
+  int32_t exp_approx; /* 1: every exponential of the rates is exp*(x) = (1 + x/1024)^1024
+                         (eq:apx-e-function) */
 } orc_params;
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
@@ -81,9 +85,33 @@ static double vtrap(double x, double k) {
   return x / (-expm1(-x / k));
 }
 
+/* exp*(x) = (1 + x/1024)^1024, evaluated as one addition and ten squarings
+ * (eq:apx-e-function). */
+double orc_exp_star(double x) {
+  double y = 1.0 + x / 1024.0;
+  for (int i = 0; i < 10; ++i) y = y * y;
+  return y;
+}
+
+/* x / (1 - exp*(-x/k)), the same shape with exp* (limit k at x = 0). */
+static double vtrap_star(double x, double k) {
+  if (x == 0.0) return k;
+  return x / (1.0 - orc_exp_star(-x / k));
+}
+
 /* out = {alpha_m, beta_m, alpha_h, beta_h, alpha_n, beta_n} in 1/ms at V. */
 void orc_hh_rates(const orc_params* p, double V, double out[6]) {
   const double u = V - p->Vrest;
+  if (p->exp_approx) {
+    /* the same formulas with each exponential replaced by exp* */
+    out[0] = 0.1 * vtrap_star(u - 25.0, 10.0);
+    out[1] = 4.0 * orc_exp_star(-u / 18.0);
+    out[2] = 0.07 * orc_exp_star(-u / 20.0);
+    out[3] = 1.0 / (1.0 + orc_exp_star((30.0 - u) / 10.0));
+    out[4] = 0.01 * vtrap_star(u - 10.0, 10.0);
+    out[5] = 0.125 * orc_exp_star(-u / 80.0);
+    return;
+  }
   out[0] = 0.1 * vtrap(u - 25.0, 10.0);          /* alpha_m */
   out[1] = 4.0 * exp(-u / 18.0);                 /* beta_m  */
   out[2] = 0.07 * exp(-u / 20.0);                /* alpha_h */

@@ -431,6 +431,57 @@ def test_invalid_schemes_are_rejected():
 
 
 # --------------------------------------------------------------------------
+# The approximated exponential exp* (eq:apx-e-function)
+# --------------------------------------------------------------------------
+
+def test_exp_star_error_matches_the_thesis_bound():
+    g = golden("exp_star_bound.txt")
+    for x in (-g["x_max"], g["x_max"]):
+        rel = abs(oracle.exp_star(x) / np.exp(x) - 1.0)
+        # below the printed bound, and not far below it: n = 2048 would give
+        # about 0.035 and n = 512 about 0.13
+        assert 0.06 < rel < g["rel_error_bound"], (x, rel)
+    assert oracle.exp_star(0.0) == 1.0
+
+
+def test_exp_star_is_the_1024th_power_of_its_base():
+    # ln exp*(x) = n log1p(x/n): an independent route through log1p
+    for x in np.linspace(-12.0, 12.0, 49):
+        assert abs(np.log(oracle.exp_star(x)) - 1024.0 * np.log1p(x / 1024.0)) <= 1e-12 * max(1.0, abs(x))
+
+
+def test_exp_star_rates_keep_their_limits_and_rest_is_exact():
+    p = P(exp_approx=1)
+    r = oracle.hh_rates(p, p["Vrest"] + 25.0)
+    assert abs(r[0] - 1.0) < 1e-15           # alpha_m at its removable singularity
+    r = oracle.hh_rates(p, p["Vrest"] + 10.0)
+    assert abs(r[4] - 0.1) < 1e-15           # alpha_n at its removable singularity
+    r0 = oracle.hh_rates(p, p["Vrest"])
+    assert r0[1] == 4.0 and r0[2] == 0.07 and r0[5] == 0.125   # exp*(0) = 1
+    # the derived leak reversal makes rest exact for the approximated rates too
+    y = np.array([p["Vrest"], *oracle.gates_inf(p, p["Vrest"])])
+    assert np.max(np.abs(oracle.hh_rhs(p, y))) <= 1e-13
+    # and it differs (slightly) from the exact-exponential one
+    d = oracle.leak_reversal_exact(p) - oracle.leak_reversal_exact(P())
+    assert 1e-5 < abs(d) < 0.01, d
+
+
+def test_exp_star_model_tracks_the_exact_model():
+    # the thesis uses exp* as a speed-for-accuracy trade; on a propagating
+    # action potential it moves V by well under a millivolt
+    n, t_end = 401, 4.0
+    out = {}
+    for apx in (0, 1):
+        p = P(exp_approx=apx)
+        st = oracle.init_state(p, n, None)
+        out[apx] = oracle.run(p, [n], [0], [n // 2], [0, 1], np.array([0.0]), st, 0,
+                              int(round(t_end / p["dt_split"])), sample_every=1)
+    assert out[0].max() > 0 and out[1].max() > 0
+    d = np.max(np.abs(out[1] - out[0]))
+    assert 0.01 < d < 1.5, d
+
+
+# --------------------------------------------------------------------------
 # Propagation velocity (sec:action_potential_velocity)
 # --------------------------------------------------------------------------
 
