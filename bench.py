@@ -128,7 +128,7 @@ class ClockSampler:
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("split_step.cu", "hh_device.cuh", "fibers_internal.h"):
+    for name in ("split_step_kernel.cuh", "split_step.cu", "hh_device.cuh", "fibers_internal.h"):
         with open(os.path.join(ROOT, "paper_2107_07104_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -341,6 +341,7 @@ def run_gpu(args, world, rank, local, dist):
     sur = None if args.no_surrogate else surrogate_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     adaptive = None if args.no_adaptive else adaptive_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     schemes = None if args.no_schemes else schemes_leg(args, w, tune, stream, dev, total)
+    expapx = None if args.no_exp_approx else exp_approx_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
@@ -371,6 +372,7 @@ def run_gpu(args, world, rank, local, dist):
         "surrogate": sur,
         "adaptive": adaptive,
         "schemes": schemes,
+        "exp_approx": expapx,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -411,31 +413,76 @@ def surrogate_leg(args, w, tune, stream, dev, total, plain_rate):
     _, fb1 = fib.stats()
     fib.close()
     rate = float(total) * args.steps / (ms / 1e3)
-    firing = [f for f in range(w.n_fibers) if w.mu_offsets[w.mu_of_fiber[f] + 1] > w.mu_offsets[w.mu_of_fiber[f]]]
-    sub = w.subset(np.sort(np.random.default_rng(9).choice(firing, min(64, len(firing)), replace=False)))
-    every = 10
-    traj = {}
-    for mode in (F.FIB_MODE_FP32, F.FIB_MODE_SURROGATE):
-        with F.Fibers.from_workload(sub, mode=mode) as f:
-            if mode == F.FIB_MODE_SURROGATE:
-                F.fibers_load_surrogate(f.ctx, blob)
-            rows = []
-            for _ in range(sub.n_steps // every):
-                f.step(every)
-                rows.append(f.read_vm().astype(np.float64))
-            traj[mode] = np.array(rows)
-    a, b = traj[F.FIB_MODE_FP32], traj[F.FIB_MODE_SURROGATE]
-    ta, tb = activation_times(a, every * sub.params["dt_split"]), activation_times(b, every * sub.params["dt_split"])
-    both = ~np.isnan(ta) & ~np.isnan(tb)
+    sub = firing_subset(w)
+    acc = agreement(trajectory(sub), trajectory(sub, mode=F.FIB_MODE_SURROGATE, blob=blob), sub)
     return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
             "network_fraction_of_node_updates": 1.0 - (fb1 - fb0) / (float(total) * args.steps),
-            "accuracy_vs_plain_fp32": {
-                "fibers": int(sub.n_fibers), "simulated_ms": sub.n_steps * sub.params["dt_split"],
-                "activation_time_max_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
-                "activated_nodes": int((~np.isnan(ta)).sum()), "matched_nodes": int(both.sum()),
-                "rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(a)),
-                "max_abs_mv": float(np.max(np.abs(a - b)))},
+            "accuracy_vs_plain_fp32": acc,
             "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}
+
+
+def firing_subset(w, n=64, seed=9):
+    """n fibers of the bundle whose motor unit fires (the accuracy sample)."""
+    firing = [f for f in range(w.n_fibers) if w.mu_offsets[w.mu_of_fiber[f] + 1] > w.mu_offsets[w.mu_of_fiber[f]]]
+    return w.subset(np.sort(np.random.default_rng(seed).choice(firing, min(n, len(firing)), replace=False)))
+
+
+TRAJ_EVERY = 10
+
+
+def trajectory(sub, mode=None, blob=None, **params):
+    """V of every node of ``sub`` every TRAJ_EVERY split steps over its whole
+    horizon, through the GPU path (FP32 unless ``mode``), with parameter
+    overrides."""
+    from paper_2107_07104_gb300 import fibers as F
+    ws = sub.with_steps(sub.n_steps)
+    ws.params = dict(sub.params, **params)
+    with F.Fibers.from_workload(ws, mode=F.FIB_MODE_FP32 if mode is None else mode) as f:
+        if blob is not None:
+            F.fibers_load_surrogate(f.ctx, blob)
+        rows = []
+        for _ in range(ws.n_steps // TRAJ_EVERY):
+            f.step(TRAJ_EVERY)
+            rows.append(f.read_vm().astype(np.float64))
+    return np.array(rows)
+
+
+def agreement(a, b, sub):
+    """How closely trajectory b follows the reference trajectory a."""
+    dt = TRAJ_EVERY * sub.params["dt_split"]
+    ta, tb = activation_times(a, dt), activation_times(b, dt)
+    both = ~np.isnan(ta) & ~np.isnan(tb)
+    return {"fibers": int(sub.n_fibers), "simulated_ms": sub.n_steps * sub.params["dt_split"],
+            "activation_time_max_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
+            "activated_nodes": int((~np.isnan(ta)).sum()), "matched_nodes": int(both.sum()),
+            "rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(a)),
+            "max_abs_mv": float(np.max(np.abs(a - b)))}
+
+
+def exp_approx_leg(args, w, tune, stream, dev, total, plain_rate):
+    """The thesis's exp* approximation (eq:apx-e-function) on the same
+    bundle: node-updates/s, and its agreement with the exact-exponential FP32
+    path on the surrogate's 64-fiber, 20 ms accuracy sample."""
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+    wa = w.with_steps(w.n_steps)
+    wa.params = dict(w.params, exp_approx=1)
+    with F.Fibers.from_workload(wa, tuning=tune, stream=stream) as fib:
+        fib.step(args.warmup)
+        fib.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        fib.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    rate = float(total) * args.steps / (ms / 1e3)
+    sub = firing_subset(w)
+    return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
+            "accuracy_vs_plain_fp32": agreement(trajectory(sub), trajectory(sub, exp_approx=1), sub),
+            "exp": "exp*(x) = (1 + x/1024)^1024 for every exponential of the rates (FP32 pipe, no ex2)"}
 
 
 def adaptive_leg(args, w, tune, stream, dev, total, plain_rate):
@@ -537,6 +584,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
+    ap.add_argument("--no-exp-approx", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

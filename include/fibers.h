@@ -72,7 +72,14 @@ enum {
    * relative) and whose motor unit has no stimulus pulse overlapping the next
    * launch is not computed during that launch (steps_per_launch split steps).
    * All fibers start active.  Not available with FIB_MODE_SURROGATE. */
-  FIB_FLAG_ADAPTIVE = 1
+  FIB_FLAG_ADAPTIVE = 1,
+  /* The thesis's approximated exponential (eq:apx-e-function): every
+   * exponential of the HH rate formulas is evaluated as exp*(x) =
+   * (1 + x/1024)^1024, on the FP32 pipe instead of the special-function
+   * unit.  It changes the model (relative error of exp* below 0.07 for
+   * |x| < 12), so the rest state and the derived leak reversal follow the
+   * approximated rates.  FIB_MODE_FP32 only. */
+  FIB_FLAG_EXP_APPROX = 2
 };
 
 /* Operator-splitting orderings (fib_params.splitting).  The splitting

@@ -114,12 +114,25 @@ void dfree(T*& p) {
 
 // ---- model constants (double precision, host) ----------------------------
 
-double vtrap(double x, double k) { return x == 0.0 ? k : x / (-std::expm1(-x / k)); }
+// exp*(x) = (1 + x/1024)^1024 (eq:apx-e-function), or exp(x).
+double rate_exp(double x, bool apx) {
+  if (!apx) return std::exp(x);
+  double y = 1.0 + x / 1024.0;
+  for (int i = 0; i < 10; ++i) y *= y;
+  return y;
+}
 
-void rest_gates(double u, double* m, double* h, double* n) {
-  const double am = 0.1 * vtrap(u - 25.0, 10.0), bm = 4.0 * std::exp(-u / 18.0);
-  const double ah = 0.07 * std::exp(-u / 20.0), bh = 1.0 / (1.0 + std::exp((30.0 - u) / 10.0));
-  const double an = 0.01 * vtrap(u - 10.0, 10.0), bn = 0.125 * std::exp(-u / 80.0);
+// x / (1 - exp(-x/k)) with its limit k at x = 0.
+double vtrap(double x, double k, bool apx) {
+  if (x == 0.0) return k;
+  return apx ? x / (1.0 - rate_exp(-x / k, true)) : x / (-std::expm1(-x / k));
+}
+
+// Steady-state gates at depolarisation u, with exact or approximated exponentials.
+void rest_gates(double u, double* m, double* h, double* n, bool apx) {
+  const double am = 0.1 * vtrap(u - 25.0, 10.0, apx), bm = 4.0 * rate_exp(-u / 18.0, apx);
+  const double ah = 0.07 * rate_exp(-u / 20.0, apx), bh = 1.0 / (1.0 + rate_exp((30.0 - u) / 10.0, apx));
+  const double an = 0.01 * vtrap(u - 10.0, 10.0, apx), bn = 0.125 * rate_exp(-u / 80.0, apx);
   *m = am / (am + bm);
   *h = ah / (ah + bh);
   *n = an / (an + bn);
@@ -150,8 +163,10 @@ fib_status validate(const fib_params* p) {
     return fail(nullptr, FIB_EINVAL, "stim_half_width must be in [0, 8]");
   if (p->mode != FIB_MODE_FP32 && p->mode != FIB_MODE_FP64_THOMAS && p->mode != FIB_MODE_SURROGATE)
     return fail(nullptr, FIB_EINVAL, "unknown mode %d", p->mode);
-  if ((p->flags & ~FIB_FLAG_ADAPTIVE) != 0 || p->reserved != 0)
+  if ((p->flags & ~(FIB_FLAG_ADAPTIVE | FIB_FLAG_EXP_APPROX)) != 0 || p->reserved != 0)
     return fail(nullptr, FIB_EINVAL, "unknown flags or nonzero reserved field");
+  if ((p->flags & FIB_FLAG_EXP_APPROX) && p->mode != FIB_MODE_FP32)
+    return fail(nullptr, FIB_EINVAL, "the exp* approximation runs in FIB_MODE_FP32 only");
   if ((p->flags & FIB_FLAG_ADAPTIVE) && p->mode == FIB_MODE_SURROGATE)
     return fail(nullptr, FIB_EINVAL, "adaptive computation is not available in surrogate mode");
   if (p->splitting < FIB_SPLIT_STRANG_1D0D1D || p->splitting > FIB_SPLIT_GODUNOV_0D1D)
@@ -373,7 +388,7 @@ HHConst hh_const(const fib_params& p, double EL) {
 
 double exact_leak_reversal(const fib_params& p) {
   double m0, h0, n0;
-  rest_gates(0.0, &m0, &h0, &n0);
+  rest_gates(0.0, &m0, &h0, &n0, (p.flags & FIB_FLAG_EXP_APPROX) != 0);
   const double ina = p.gNa * m0 * m0 * m0 * h0 * (p.Vrest - p.ENa);
   const double ik = p.gK * n0 * n0 * n0 * n0 * (p.Vrest - p.EK);
   return p.Vrest + (ina + ik) / p.gL;
@@ -404,6 +419,7 @@ StepArgs make_args(fib_ctx* c) {
     default: a.k_split = a.n_sub; a.n_cn2 = 0; break;  // FIB_SPLIT_GODUNOV_0D1D
   }
   a.implicit_euler = c->p.diffusion == FIB_DIFFUSION_IMPLICIT_EULER ? 1 : 0;
+  a.exp_approx = (c->p.flags & FIB_FLAG_EXP_APPROX) ? 1 : 0;
   a.pulse = (int32_t)c->pulse;
   a.hw = c->p.stim_half_width;
   a.n_mu = c->n_mu;
@@ -631,7 +647,7 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
   // r = c dt_1d / h^2 gives the CN left-hand side, twice that the implicit
   // Euler one.
   c->r = (p->diffusion == FIB_DIFFUSION_IMPLICIT_EULER ? 2.0 : 1.0) * cdiff * p->dt_1d / (p->h * p->h);
-  rest_gates(0.0, &c->m0, &c->h0, &c->n0);
+  rest_gates(0.0, &c->m0, &c->h0, &c->n0, (p->flags & FIB_FLAG_EXP_APPROX) != 0);
   if (std::isnan(p->EL)) {
     const double ina = p->gNa * c->m0 * c->m0 * c->m0 * c->h0 * (p->Vrest - p->ENa);
     const double ik = p->gK * c->n0 * c->n0 * c->n0 * c->n0 * (p->Vrest - p->EK);

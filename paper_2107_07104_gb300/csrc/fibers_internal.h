@@ -76,6 +76,7 @@ struct StepArgs {
   int32_t n_cn;            // diffusion steps of the first diffusion phase
   int32_t n_cn2;           // diffusion steps of the second diffusion phase
   int32_t implicit_euler;  // 1: right-hand side u (eq:lumping_implicit_euler_2); 0: CN
+  int32_t exp_approx;      // 1: rates with exp* (eq:apx-e-function), FP32 solve only
   int32_t pulse;           // stimulus length in substeps
   int32_t hw;              // stimulus half width (nodes)
   int32_t n_mu;
@@ -112,6 +113,8 @@ bool build_solver_tables(int K, double r, const std::vector<int32_t>& lengths,
 
 // Device entry points (split_step.cu).
 int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
+// The exp* instantiations (split_step_expapx.cu).
+int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream);
 int launch_advance(int64_t* step_base, int64_t n, void* stream);
 // dst[coff + i] = src[slot + i] + add for the n real nodes of every fiber.
 int launch_gather(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,

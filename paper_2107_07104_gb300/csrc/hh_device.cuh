@@ -68,18 +68,59 @@ struct Deriv {
   float u, m, h, n;
 };
 
+// The thesis's approximated exponential exp*(x) = (1 + x/1024)^1024
+// (eq:apx-e-function): one FMA (x/1024 is exact) and ten squarings, all on
+// the FP32 pipe instead of the special-function unit.
+__device__ __forceinline__ float exp_star(float x) {
+  float y = fmaf(x, 1.0f / 1024.0f, 1.0f);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) y = y * y;
+  return y;
+}
+
+// The exponential terms of the rates.  Exact form: one ex2 gives
+// E = e^(-u/10) and the three /10 rates reuse it through e^2.5, e and e^3.
+// EXPAPX: each exponential of the rate formulas becomes its own exp*, since
+// exp* is not multiplicative.  Returns the quotient denominators
+// e^((25-u)/10) - 1, e^((10-u)/10) - 1, -e^((30-u)/10) - 1 and the scaled
+// exponentials beta_m, alpha_h, beta_n.
+struct RateExps {
+  float dm, dn, dh, bm, ah, bn;
+};
+
+template <bool EXPAPX>
+__device__ __forceinline__ RateExps rate_exps(float u, float nzm, float nzn) {
+  RateExps r;
+  if (EXPAPX) {
+    r.dm = exp_star(-nzm) - 1.0f;                              // (25 - u)/10 = -nzm
+    r.dn = exp_star(fmaf(u, -0.1f, 1.0f)) - 1.0f;              // (10 - u)/10
+    r.dh = fmaf(exp_star(fmaf(u, -0.1f, 3.0f)), -1.0f, -1.0f);
+    r.bm = 4.0f * exp_star(u * (-1.0f / 18.0f));
+    r.ah = 0.07f * exp_star(u * (-1.0f / 20.0f));
+    r.bn = 0.125f * exp_star(u * (-1.0f / 80.0f));
+  } else {
+    const float E = ex2_approx(u * (-kLog2e / 10.0f));
+    r.bm = ex2_approx(fmaf(u, -kLog2e / 18.0f, 2.0f));                    // 4 e^(-u/18)
+    r.ah = ex2_approx(fmaf(u, -kLog2e / 20.0f, -3.8365012677171206f));    // 0.07 e^(-u/20)
+    r.bn = ex2_approx(fmaf(u, -kLog2e / 80.0f, -3.0f));                   // 0.125 e^(-u/80)
+    r.dm = fmaf(kE25, E, -1.0f);
+    r.dn = fmaf(kE10, E, -1.0f);
+    r.dh = fmaf(-kE30, E, -1.0f);
+  }
+  return r;
+}
+
+template <bool EXPAPX = false>
 __device__ __forceinline__ Deriv hh_rhs(float u, float m, float h, float n, float gl_ul, const HHConst& c) {
-  const float E = ex2_approx(u * (-kLog2e / 10.0f));
-  const float bm = ex2_approx(fmaf(u, -kLog2e / 18.0f, 2.0f));                    // 4 e^(-u/18)
-  const float ah = ex2_approx(fmaf(u, -kLog2e / 20.0f, -3.8365012677171206f));    // 0.07 e^(-u/20)
-  const float bn = ex2_approx(fmaf(u, -kLog2e / 80.0f, -3.0f));                   // 0.125 e^(-u/80)
   const float nzm = fmaf(u, 0.1f, -2.5f);    // -(25 - u) / 10
   const float nzn = fmaf(u, 0.01f, -0.1f);   // -(10 - u) / 100
+  const RateExps x = rate_exps<EXPAPX>(u, nzm, nzn);
+  const float bm = x.bm, ah = x.ah, bn = x.bn;
   // branch-free (a branch would split the unrolled node loop into blocks
   // the scheduler cannot interleave)
-  const float nam = fabsf(nzm) < 0.01f ? nam_series(nzm) : nzm * rcp_approx(fmaf(kE25, E, -1.0f));
-  const float nan_ = fabsf(nzn) < 0.001f ? nan_series(nzn) : nzn * rcp_approx(fmaf(kE10, E, -1.0f));
-  const float nbh = rcp_approx(fmaf(-kE30, E, -1.0f));
+  const float nam = fabsf(nzm) < 0.01f ? nam_series(nzm) : nzm * rcp_approx(x.dm);
+  const float nan_ = fabsf(nzn) < 0.001f ? nan_series(nzn) : nzn * rcp_approx(x.dn);
+  const float nbh = rcp_approx(x.dh);
   Deriv d;
   d.m = fmaf(bm - nam, m, nam);     // (am + bm) m - am
   d.h = fmaf(nbh - ah, h, ah);      // ah - (ah + bh) h
@@ -96,14 +137,14 @@ __device__ __forceinline__ Deriv hh_rhs(float u, float m, float h, float n, floa
 // One Heun substep (eq:heun) of every node a thread holds.  STIM: the
 // thread owns at least one junction node and the pulse is on; `mask` has
 // bit j set for stimulated nodes.
-template <int K, bool STIM>
+template <int K, bool STIM, bool EXPAPX = false>
 __device__ __forceinline__ void heun_nodes(float (&u)[K], float (&m)[K], float (&h)[K], float (&n)[K],
                                            const HHConst& c, uint32_t mask) {
   const float dt = c.dt0, hdt = 0.5f * c.dt0;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const float s = (STIM && ((mask >> j) & 1u)) ? c.gL_uL + c.stim : c.gL_uL;
-    const Deriv f0 = hh_rhs(u[j], m[j], h[j], n[j], s, c);
+    const Deriv f0 = hh_rhs<EXPAPX>(u[j], m[j], h[j], n[j], s, c);
     const float u1 = fmaf(dt, f0.u, u[j]);
     const float m1 = fmaf(-dt, f0.m, m[j]);
     const float h1 = fmaf(dt, f0.h, h[j]);
@@ -114,7 +155,7 @@ __device__ __forceinline__ void heun_nodes(float (&u)[K], float (&m)[K], float (
     m[j] = fmaf(-hdt, f0.m, m[j]);
     h[j] = fmaf(hdt, f0.h, h[j]);
     n[j] = fmaf(-hdt, f0.n, n[j]);
-    const Deriv f1 = hh_rhs(u1, m1, h1, n1, s, c);
+    const Deriv f1 = hh_rhs<EXPAPX>(u1, m1, h1, n1, s, c);
     u[j] = fmaf(hdt, f1.u, u[j]);
     m[j] = fmaf(-hdt, f1.m, m[j]);
     h[j] = fmaf(hdt, f1.h, h[j]);

@@ -1,0 +1,20 @@
+// Split-step kernel instantiations with the thesis's approximated
+// exponential exp*(x) = (1 + x/1024)^1024 (eq:apx-e-function) in place of
+// every exponential of the Hodgkin-Huxley rates; FP32 solve only.  Kept in
+// its own translation unit so that it compiles in parallel with the exact
+// instantiations.
+#include "split_step_kernel.cuh"
+
+namespace fib {
+
+int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream) {
+  switch (K) {
+    case 4: return launch_k<4, float, true>(a, n_ctas, stream);
+    case 8: return launch_k<8, float, true>(a, n_ctas, stream);
+    case 12: return launch_k<12, float, true>(a, n_ctas, stream);
+    case 16: return launch_k<16, float, true>(a, n_ctas, stream);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fib

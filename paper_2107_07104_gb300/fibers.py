@@ -25,6 +25,7 @@ _lock = threading.Lock()
 FIB_OK, FIB_EINVAL, FIB_ENOMEM, FIB_ECUDA, FIB_ENONFINITE, FIB_ETIMEOUT, FIB_ESTATE, FIB_ENOTSUP = range(8)
 FIB_MODE_FP32, FIB_MODE_FP64_THOMAS, FIB_MODE_SURROGATE = 0, 1, 2
 FIB_FLAG_ADAPTIVE = 1
+FIB_FLAG_EXP_APPROX = 2
 SPLIT_STRANG_1D0D1D, SPLIT_GODUNOV_1D0D, SPLIT_STRANG_0D1D0D, SPLIT_GODUNOV_0D1D = 0, 1, 2, 3
 DIFFUSION_CRANK_NICOLSON, DIFFUSION_IMPLICIT_EULER = 0, 1
 STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINITE", "FIB_ETIMEOUT",
@@ -140,7 +141,7 @@ def make_params(p: dict, mode: int = FIB_MODE_FP32) -> FibParams:
         setattr(o, k, float(p[k]))
     o.stim_half_width = int(p.get("stim_half_width", 1))
     o.mode = int(p.get("mode", mode))
-    o.flags = int(p.get("flags", 0))
+    o.flags = int(p.get("flags", 0)) | (FIB_FLAG_EXP_APPROX if p.get("exp_approx", 0) else 0)
     o.splitting = int(p.get("splitting", SPLIT_STRANG_1D0D1D))
     o.diffusion = int(p.get("diffusion", DIFFUSION_CRANK_NICOLSON))
     o.reserved = 0

@@ -56,6 +56,7 @@ DEFAULT_PARAMS = dict(
     stim_half_width=1,     # nodes j-1..j+1
     splitting=0,           # Strang, diffusion dt/2 - reaction dt - diffusion dt/2
     diffusion=0,           # Crank-Nicolson
+    exp_approx=0,          # 1: rates use exp*(x) = (1 + x/1024)^1024 instead of exp
 )
 
 

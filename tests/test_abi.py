@@ -72,6 +72,8 @@ def _create(**over):
     (dict(splitting=1, dt_1d=0.002), "whole numbers"),     # Godunov diffuses over the whole dt_split
     (dict(splitting=3, mode=F.FIB_MODE_SURROGATE), "surrogate mode runs only"),
     (dict(diffusion=1, mode=F.FIB_MODE_SURROGATE), "surrogate mode runs only"),
+    (dict(exp_approx=1, mode=F.FIB_MODE_FP64_THOMAS), "FIB_MODE_FP32 only"),
+    (dict(exp_approx=1, mode=F.FIB_MODE_SURROGATE), "FIB_MODE_FP32 only"),
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, over, text):
     with pytest.raises(F.FibersError) as ei:
