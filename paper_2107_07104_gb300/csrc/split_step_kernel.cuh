@@ -208,8 +208,12 @@ struct Exchange {  // per-CTA shared buffers, one element per thread
 };
 
 // Per-thread reduced-system coefficients, kept in shared memory (one column
-// per thread, row k at cf[k * B]) rather than in registers.
+// per thread, row k at cf[k * kStride]) rather than in registers.  The
+// exchange buffers and this table use the fixed stride kStride (the largest
+// CTA) rather than blockDim.x, so every shared-memory address in the solve is
+// the thread's own offset plus an immediate.
 enum { kInvB = 0, kAb, kCb, kC0, kKE, kKD, kKDn, kPKE, kPKD, kPKDn, kNumCoef };
+constexpr int kStride = 32 * kMaxWarpsPerCta;
 
 template <int K, typename R>
 struct SolveCtx {
@@ -217,7 +221,7 @@ struct SolveCtx {
   const R* rec;  // this thread's reduced-system record (global memory)
   const R* cf;   // this thread's column of the coefficient table (shared memory)
   R r;           // c dt_1d / h^2 (0 for single-node fibers)
-  int p, Tw, tid, B, nreal, bar_id, levels;
+  int p, Tw, tid, nreal, bar_id, levels;
   bool edge;     // chunk holds the fiber's last row or padding
   bool ie;       // implicit Euler: right-hand side is u itself
 };
@@ -264,7 +268,7 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
   // back substitution towards the chunk's first row
 #pragma unroll
   for (int j = K - 3; j >= 1; --j) d[j] = d[j] - s.set[j * kCoefPerRow + 2] * d[j + 1];
-  const R D = d[0] - s.cf[kC0 * s.B] * d[1];
+  const R D = d[0] - s.cf[kC0 * kStride] * d[1];
   const R E = d[K - 1];
   R y, ym;
   if (s.levels == 0) {
@@ -276,20 +280,20 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
     x.E[s.tid] = E;
     fiber_barrier(s.bar_id, s.Tw);
     const R Dn = (s.p + 1 < s.Tw) ? x.D[s.tid + 1] : (R)0;
-    y = E * s.cf[kKE * s.B] - s.cf[kKD * s.B] * D - s.cf[kKDn * s.B] * Dn;
+    y = E * s.cf[kKE * kStride] - s.cf[kKD * kStride] * D - s.cf[kKDn * kStride] * Dn;
     ym = (R)0;
     if (s.p > 0) {
       const R Dp = x.D[s.tid - 1], Ep = x.E[s.tid - 1];
-      ym = Ep * s.cf[kPKE * s.B] - s.cf[kPKD * s.B] * Dp - s.cf[kPKDn * s.B] * D;
+      ym = Ep * s.cf[kPKE * kStride] - s.cf[kPKD * kStride] * Dp - s.cf[kPKDn * kStride] * D;
     }
   } else {
     x.D[s.tid] = D;
     fiber_barrier(s.bar_id, s.Tw);
     const R Dn = (s.p + 1 < s.Tw) ? x.D[s.tid + 1] : (R)0;
-    R rr = E * s.cf[kKE * s.B] - s.cf[kKD * s.B] * D - s.cf[kKDn * s.B] * Dn;
+    R rr = E * s.cf[kKE * kStride] - s.cf[kKD * kStride] * D - s.cf[kKDn * kStride] * Dn;
     // parallel cyclic reduction over the chunks' last unknowns
     for (int l = 0, st = 1; l < s.levels; ++l, st <<= 1) {
-      R* buf = x.r2 + (l & 1) * s.B;
+      R* buf = x.r2 + (l & 1) * kStride;
       buf[s.tid] = rr;
       fiber_barrier(s.bar_id, s.Tw);
       const R rm = (s.p - st >= 0) ? buf[s.tid - st] : (R)0;
@@ -302,7 +306,7 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
     fiber_barrier(s.bar_id, s.Tw);
     ym = (s.p > 0) ? x.y[s.tid - 1] : (R)0;
   }
-  const R xs = D * s.cf[kInvB * s.B] - s.cf[kAb * s.B] * ym - s.cf[kCb * s.B] * y;
+  const R xs = D * s.cf[kInvB * kStride] - s.cf[kAb * kStride] * ym - s.cf[kCb * kStride] * y;
   u[0] = (float)xs;
   u[K - 1] = (float)y;
 #pragma unroll
@@ -327,13 +331,13 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   R* s_rows = reinterpret_cast<R*>(smem_raw);  // interior set + one last set per CTA fiber
   Exchange<R> x;
   x.first = s_rows + (1 + kMaxFibersPerCta) * set_len;
-  x.last = x.first + B;
-  x.D = x.last + B;
-  x.E = x.D + B;
-  x.y = x.E + B;
-  x.r2 = x.y + B;
-  R* s_coef = x.r2 + 2 * B;  // kNumCoef x B
-  float* s_keep = reinterpret_cast<float*>(s_coef + kNumCoef * B);  // adaptive: 4 K x B state copy
+  x.last = x.first + kStride;
+  x.D = x.last + kStride;
+  x.E = x.D + kStride;
+  x.y = x.E + kStride;
+  x.r2 = x.y + kStride;
+  R* s_coef = x.r2 + 2 * kStride;  // kNumCoef x kStride
+  float* s_keep = reinterpret_cast<float*>(s_coef + kNumCoef * kStride);  // adaptive: 4 K x B state copy
   int* s_eq = reinterpret_cast<int*>(s_keep + (a.adaptive ? 4 * K * B : 0));  // adaptive: one per warp
 
   const WarpMap wm = a.warps[(int64_t)blockIdx.x * a.W + warp];
@@ -358,7 +362,6 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   sc.p = p;
   sc.Tw = Tw;
   sc.tid = tid;
-  sc.B = B;
   sc.nreal = nreal;
   sc.bar_id = wm.slot + 1;
   sc.levels = a.n_levels;
@@ -368,10 +371,10 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   sc.ie = a.implicit_euler != 0;
   const R* g_recs = static_cast<const R*>(a.recs);
   sc.rec = g_recs + fd.rec + (int64_t)p * a.rec_stride;
-  for (int k = 0; k < 7; ++k) s_coef[k * B + tid] = sc.rec[k];
-  s_coef[kPKE * B + tid] = p > 0 ? sc.rec[4 - a.rec_stride] : (R)0;
-  s_coef[kPKD * B + tid] = p > 0 ? sc.rec[5 - a.rec_stride] : (R)0;
-  s_coef[kPKDn * B + tid] = p > 0 ? sc.rec[6 - a.rec_stride] : (R)0;
+  for (int k = 0; k < 7; ++k) s_coef[k * kStride + tid] = sc.rec[k];
+  s_coef[kPKE * kStride + tid] = p > 0 ? sc.rec[4 - a.rec_stride] : (R)0;
+  s_coef[kPKD * kStride + tid] = p > 0 ? sc.rec[5 - a.rec_stride] : (R)0;
+  s_coef[kPKDn * kStride + tid] = p > 0 ? sc.rec[6 - a.rec_stride] : (R)0;
   sc.cf = s_coef + tid;  // own column: read back only by this thread
 
   // load this thread's K nodes (vectorised: slot and K are multiples of 4)
