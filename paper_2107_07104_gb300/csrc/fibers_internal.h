@@ -113,8 +113,10 @@ bool build_solver_tables(int K, double r, const std::vector<int32_t>& lengths,
 
 // Device entry points (split_step.cu).
 int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
-// The exp* instantiations (split_step_expapx.cu).
+// The exp* instantiations (split_step_expapx.cu) and the adaptive ones
+// (split_step_adaptive.cu).
 int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream);
+int launch_split_step_adaptive(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
 int launch_advance(int64_t* step_base, int64_t n, void* stream);
 // dst[coff + i] = src[slot + i] + add for the n real nodes of every fiber.
 int launch_gather(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,

@@ -8,13 +8,8 @@
 namespace fib {
 
 int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream) {
-  switch (K) {
-    case 4: return launch_k<4, float, true>(a, n_ctas, stream);
-    case 8: return launch_k<8, float, true>(a, n_ctas, stream);
-    case 12: return launch_k<12, float, true>(a, n_ctas, stream);
-    case 16: return launch_k<16, float, true>(a, n_ctas, stream);
-    default: return (int)cudaErrorInvalidValue;
-  }
+  return a.adaptive ? launch_family<float, true, true>(K, a, n_ctas, stream)
+                    : launch_family<float, true, false>(K, a, n_ctas, stream);
 }
 
 }  // namespace fib

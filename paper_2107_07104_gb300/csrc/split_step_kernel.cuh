@@ -320,7 +320,10 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
 
 // MINB: CTAs of up to 256 threads that must fit on one SM at once; it sets
 // the register budget (2: up to 128 registers per thread, 3: up to 85).
-template <int K, typename R, bool PACKED, int MINB, bool EXPAPX>
+// ADAPT: adaptive computation (sec:adaptive_computation_for_fiber_based):
+// a fiber in equilibrium with no pulse due skips a whole launch.  Only the
+// adaptive instantiations carry its code.
+template <int K, typename R, bool PACKED, int MINB, bool EXPAPX, bool ADAPT>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
     split_step_kernel(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -337,8 +340,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   x.y = x.E + kStride;
   x.r2 = x.y + kStride;
   R* s_coef = x.r2 + 2 * kStride;  // kNumCoef x kStride
-  float* s_keep = reinterpret_cast<float*>(s_coef + kNumCoef * kStride);  // adaptive: 4 K x B state copy
-  int* s_eq = reinterpret_cast<int*>(s_keep + (a.adaptive ? 4 * K * B : 0));  // adaptive: one per warp
+  float* s_keep = reinterpret_cast<float*>(s_coef + kNumCoef * kStride);  // ADAPT: 4 K x B state copy
+  int* s_eq = reinterpret_cast<int*>(s_keep + (ADAPT ? 4 * K * B : 0));  // ADAPT: one per warp
 
   const WarpMap wm = a.warps[(int64_t)blockIdx.x * a.W + warp];
   const R* g_rows = static_cast<const R*>(a.rows);
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   }
 
   const int64_t step0 = *a.step_base + a.step_offset;
-  if (a.adaptive) {
+  if (ADAPT) {
     // Adaptive computation (sec:adaptive_computation_for_fiber_based): a
     // fiber that was in equilibrium at the end of its last launch and whose
     // motor unit has no pulse overlapping this launch is skipped whole.  The
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   const int first_half = a.phases & 1, reaction = a.phases & 2, second_half = a.phases & 4;
   for (int s = 0; s < a.n_steps; ++s) {
     const int64_t stp = step0 + s;
-    if (a.adaptive && s == a.n_steps - 1) {
+    if (ADAPT && s == a.n_steps - 1) {
 #pragma unroll
       for (int j = 0; j < K; ++j) {
         s_keep[(0 * K + j) * B + tid] = u[j];
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
       for (int c = 0; c < a.n_cn2; ++c) cn_solve<K, R>(u, sc, x);
   }
 
-  if (a.adaptive) {
+  if (ADAPT) {
     // equilibrium test over the launch's last split step: every component of
     // every real node changed by at most eq_tol relative (V taken absolute)
     bool eq = true;
@@ -517,26 +520,39 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   }
 }
 
-template <int K, typename R, bool PACKED, int MINB, bool EXPAPX>
+template <int K, typename R, bool PACKED, int MINB, bool EXPAPX, bool ADAPT>
 int launch_one(const StepArgs& a, int n_ctas, void* stream) {
-  const size_t smem = split_step_smem_bytes(K, sizeof(R) == 8, a.W, a.adaptive != 0);
+  const size_t smem = split_step_smem_bytes(K, sizeof(R) == 8, a.W, ADAPT);
   if (smem > 48 * 1024) {  // opt in to more than the default dynamic shared memory
-    const cudaError_t e = cudaFuncSetAttribute(split_step_kernel<K, R, PACKED, MINB, EXPAPX>,
+    const cudaError_t e = cudaFuncSetAttribute(split_step_kernel<K, R, PACKED, MINB, EXPAPX, ADAPT>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  split_step_kernel<K, R, PACKED, MINB, EXPAPX><<<n_ctas, 32 * a.W, smem, static_cast<cudaStream_t>(stream)>>>(a);
+  split_step_kernel<K, R, PACKED, MINB, EXPAPX, ADAPT>
+      <<<n_ctas, 32 * a.W, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <int K, typename R, bool EXPAPX>
+template <int K, typename R, bool EXPAPX, bool ADAPT>
 int launch_k(const StepArgs& a, int n_ctas, void* stream) {
-  if (sizeof(R) == 8) return launch_one<K, R, false, 2, EXPAPX>(a, n_ctas, stream);  // FP64 solve: one form
+  if (sizeof(R) == 8) return launch_one<K, R, false, 2, EXPAPX, ADAPT>(a, n_ctas, stream);  // FP64 solve: one form
   if (a.lean)
-    return a.packed ? launch_one<K, R, true, 3, EXPAPX>(a, n_ctas, stream)
-                    : launch_one<K, R, false, 3, EXPAPX>(a, n_ctas, stream);
-  return a.packed ? launch_one<K, R, true, 2, EXPAPX>(a, n_ctas, stream)
-                  : launch_one<K, R, false, 2, EXPAPX>(a, n_ctas, stream);
+    return a.packed ? launch_one<K, R, true, 3, EXPAPX, ADAPT>(a, n_ctas, stream)
+                    : launch_one<K, R, false, 3, EXPAPX, ADAPT>(a, n_ctas, stream);
+  return a.packed ? launch_one<K, R, true, 2, EXPAPX, ADAPT>(a, n_ctas, stream)
+                  : launch_one<K, R, false, 2, EXPAPX, ADAPT>(a, n_ctas, stream);
+}
+
+// Dispatch on K for one (R, EXPAPX, ADAPT) family of instantiations.
+template <typename R, bool EXPAPX, bool ADAPT>
+int launch_family(int K, const StepArgs& a, int n_ctas, void* stream) {
+  switch (K) {
+    case 4: return launch_k<4, R, EXPAPX, ADAPT>(a, n_ctas, stream);
+    case 8: return launch_k<8, R, EXPAPX, ADAPT>(a, n_ctas, stream);
+    case 12: return launch_k<12, R, EXPAPX, ADAPT>(a, n_ctas, stream);
+    case 16: return launch_k<16, R, EXPAPX, ADAPT>(a, n_ctas, stream);
+    default: return (int)cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
