@@ -70,7 +70,7 @@ struct fib_ctx {
   int64_t graph_launches = 0;
 
   // reaction-step surrogate (FIB_MODE_SURROGATE)
-  int32_t* d_slot_fiber = nullptr;   // fiber of every slot
+  int32_t* d_slot_fiber = nullptr;   // surrogate: per-slot code (fiber << 1 | stimulated), -1 padding
   uint8_t* d_fiber_stim = nullptr;   // per-fiber stimulus substep mask of the current step
   uint16_t* d_sur_wts = nullptr;     // bf16 weight images
   float* d_sur_bias = nullptr;
@@ -332,9 +332,15 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   CU(c, cudaMalloc(&c->d_recs, es * std::max<size_t>(tab.recs.size(), 1)));
   if (!fd.empty()) CU(c, cudaMemcpy(c->d_fibers, fd.data(), sizeof(FiberDesc) * fd.size(), cudaMemcpyHostToDevice));
   if (c->p.mode == FIB_MODE_SURROGATE && slot > 0) {
+    // per-slot code for the surrogate kernel: -1 padding, else
+    // (fiber << 1) | (node within the junction's stimulus range)
     std::vector<int32_t> sf((size_t)slot, -1);
-    for (int32_t f = 0; f < c->n_fibers; ++f)
-      for (int32_t i = 0; i < fd[f].slot_len; ++i) sf[(size_t)fd[f].slot + i] = f;
+    const int hw = c->p.stim_half_width;
+    for (int32_t f = 0; f < c->n_fibers; ++f) {
+      const int lo = std::max(fd[f].junction - hw, 0), hi = std::min(fd[f].junction + hw, fd[f].n - 1);
+      for (int32_t i = 0; i < fd[f].n; ++i)
+        sf[(size_t)fd[f].slot + i] = (f << 1) | ((fd[f].mu >= 0 && i >= lo && i <= hi) ? 1 : 0);
+    }
     CU(c, cudaMalloc(&c->d_slot_fiber, sizeof(int32_t) * sf.size()));
     CU(c, cudaMemcpy(c->d_slot_fiber, sf.data(), sizeof(int32_t) * sf.size(), cudaMemcpyHostToDevice));
   }
@@ -543,8 +549,7 @@ fib_status surrogate_steps(fib_ctx* c, int64_t n) {
   s.m = st_m(c);
   s.h = st_h(c);
   s.n = st_n(c);
-  s.fibers = c->d_fibers;
-  s.slot_fiber = c->d_slot_fiber;
+  s.slot_code = c->d_slot_fiber;
   s.fiber_stim = c->d_fiber_stim;
   s.wts = c->d_sur_wts;
   s.bias = c->d_sur_bias;

@@ -8,8 +8,9 @@
 //     weights and activations in the forward pass, straight-through
 //     gradients) and an Adam update;
 //   * sur_step_kernel: inference on BF16 tensor cores (mma.sync m16n8k16,
-//     FP32 accumulation) with an envelope test that sends nodes outside the
-//     training data's range to the plain HH step.
+//     FP32 accumulation) on the nodes that need it, compacted per warp into
+//     full tiles, with an envelope test that sends nodes outside the
+//     training data's range (or near rest) to the plain HH step.
 // Network: x (5) -> 128 -> SiLU -> 128 -> SiLU -> 4, predicting the change of
 // (u, m, h, n) over one split step in normalised units.
 #include <cuda_bf16.h>
@@ -267,43 +268,11 @@ __device__ __forceinline__ void to_a_frag(const float (&c0)[4], const float (&c1
   a[3] = pack_bf16(silu(c1[2] + b10), silu(c1[3] + b11));
 }
 
-struct SurNode {
-  float u, m, h, n, s;  // state and stimulus fraction
-  int fiber;            // -1: padding (no update)
-  uint32_t mask;        // stimulus substeps
-};
-
-__device__ __forceinline__ SurNode load_node(const SurArgs& a, int64_t q) {
-  SurNode r{};
-  r.fiber = -1;
-  if (q >= a.n_slots) return r;
-  const int32_t f = a.slot_fiber[q];
-  r.u = a.u[q];
-  r.m = a.m[q];
-  r.h = a.h[q];
-  r.n = a.n[q];
-  r.mask = 0u;
-  r.s = 0.0f;
-  if (f >= 0) {
-    const FiberDesc fd = a.fibers[f];
-    const int i = (int)(q - fd.slot);
-    if (i < fd.n) {
-      r.fiber = f;
-      const int lo = max(fd.junction - a.hw, 0), hi = min(fd.junction + a.hw, fd.n - 1);
-      if (i >= lo && i <= hi) {
-        r.mask = a.fiber_stim[f];
-        r.s = (float)__popc(r.mask) / (float)a.n_sub;
-      }
-    }
-  }
-  return r;
-}
-
-// The network only handles nodes inside its training envelope and away from
-// rest: near rest the exact step is cheap and keeps rest an exact fixed
-// point, which a network's small output errors would not.
-__device__ __forceinline__ bool use_plain_step(const SurArgs& a, const SurNode& v) {
-  const float raw[kIn] = {v.u, v.m, v.h, v.n, v.s};
+// Does a node take the plain HH step?  The network only handles nodes inside
+// its training envelope and away from rest: near rest the exact step is cheap
+// and keeps rest an exact fixed point, which a network's small output errors
+// would not.
+__device__ __forceinline__ bool use_plain_step(const SurArgs& a, const float (&raw)[kIn]) {
   bool outside = false, quiet = true;
 #pragma unroll
   for (int k = 0; k < kIn; ++k) {
@@ -313,119 +282,174 @@ __device__ __forceinline__ bool use_plain_step(const SurArgs& a, const SurNode& 
   return outside || quiet;
 }
 
-__global__ void __launch_bounds__(128) sur_step_kernel(const SurArgs a) {
+// Per-warp staging of the nodes that go through the network: normalised
+// features, the state before the step, and the slot.
+constexpr int kChunk = 64;  // slots per warp and iteration: two adjacent slots per lane
+constexpr int kStageFloats = kChunk * (kIn + 4 + 1);
+constexpr int kSurThreads = 128;
+
+// Inference tile: rows g and g + 8 of 16 staged nodes starting at `base`.
+__device__ __forceinline__ void network_tile(const SurArgs& a, const uint16_t* sW1, const uint16_t* sW2,
+                                             const uint16_t* sW3, const float* sB, const float* sx, const float* sy,
+                                             const int* sq, int base, int count, int g, int t) {
+  const int r0 = base + g, r1 = base + g + 8;
+  const bool ok0 = r0 < count, ok1 = r1 < count;
+  // features split into bf16 hi + lo parts (FP32-accurate inputs)
+  auto feat = [&](int r, bool ok, int col) -> float {
+    if (!ok || col >= 2 * kIn) return 0.0f;
+    const float x = sx[r * kIn + (col < kIn ? col : col - kIn)];
+    const float hi = __bfloat162float(__float2bfloat16_rn(x));
+    return col < kIn ? hi : x - hi;
+  };
+  uint32_t A1[4];
+  A1[0] = pack_bf16(feat(r0, ok0, 2 * t), feat(r0, ok0, 2 * t + 1));
+  A1[1] = pack_bf16(feat(r1, ok1, 2 * t), feat(r1, ok1, 2 * t + 1));
+  A1[2] = pack_bf16(feat(r0, ok0, 2 * t + 8), feat(r0, ok0, 2 * t + 9));
+  A1[3] = pack_bf16(feat(r1, ok1, 2 * t + 8), feat(r1, ok1, 2 * t + 9));
+  // layer 1: 16 n-tiles of 8 neurons, one k-tile
+  uint32_t A2[8][4];
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+    const uint32_t* w0 = reinterpret_cast<const uint32_t*>(sW1 + (16 * kk + g) * kW1Stride);
+    const uint32_t* w1 = reinterpret_cast<const uint32_t*>(sW1 + (16 * kk + 8 + g) * kW1Stride);
+    mma_bf16(c0, A1, w0[t], w0[t + 4]);
+    mma_bf16(c1, A1, w1[t], w1[t + 4]);
+    to_a_frag(c0, c1, sB + 16 * kk, sB + 16 * kk + 8, t, A2[kk]);
+  }
+  // layer 2: 16 n-tiles, 8 k-tiles
+  uint32_t A3[8][4];
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+    const uint32_t* w0 = reinterpret_cast<const uint32_t*>(sW2 + (16 * kk + g) * kW2Stride);
+    const uint32_t* w1 = reinterpret_cast<const uint32_t*>(sW2 + (16 * kk + 8 + g) * kW2Stride);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      mma_bf16(c0, A2[k2], w0[8 * k2 + t], w0[8 * k2 + t + 4]);
+      mma_bf16(c1, A2[k2], w1[8 * k2 + t], w1[8 * k2 + t + 4]);
+    }
+    to_a_frag(c0, c1, sB + kHid + 16 * kk, sB + kHid + 16 * kk + 8, t, A3[kk]);
+  }
+  // layer 3: one n-tile (4 outputs padded to 8), 8 k-tiles
+  float o[4] = {0, 0, 0, 0};
+  {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(sW3 + g * kW2Stride);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) mma_bf16(o, A3[k2], w[8 * k2 + t], w[8 * k2 + t + 4]);
+  }
+  // lane t = 0 holds outputs 0, 1 (du, dm) and t = 1 outputs 2, 3 (dh, dn)
+  // of rows r0 (o[0], o[1]) and r1 (o[2], o[3])
+  if (t < 2) {
+    const int k0 = 2 * t, k1 = 2 * t + 1;
+    const float b0 = sB[2 * kHid + k0], b1 = sB[2 * kHid + k1];
+    float* dst0 = k0 == 0 ? a.u : a.h;
+    float* dst1 = k1 == 1 ? a.m : a.n;
+    if (ok0) {
+      const int64_t q = sq[r0];
+      dst0[q] = sy[r0 * 4 + k0] + fmaf(o[0] + b0, a.out_sigma[k0], a.out_mu[k0]);
+      dst1[q] = sy[r0 * 4 + k1] + fmaf(o[1] + b1, a.out_sigma[k1], a.out_mu[k1]);
+    }
+    if (ok1) {
+      const int64_t q = sq[r1];
+      dst0[q] = sy[r1 * 4 + k0] + fmaf(o[2] + b0, a.out_sigma[k0], a.out_mu[k0]);
+      dst1[q] = sy[r1 * 4 + k1] + fmaf(o[3] + b1, a.out_sigma[k1], a.out_mu[k1]);
+    }
+  }
+}
+
+// One reaction step of every slot.  A warp takes 64 consecutive slots, two
+// adjacent ones per lane (same fiber: fiber slots are 4-aligned).  Nodes for
+// the plain step integrate in place, two per lane; nodes for the network are
+// compacted into the warp's staging area and evaluated 16 at a time on the
+// tensor cores, so every tile is full except the last one of a chunk.
+__global__ void __launch_bounds__(kSurThreads) sur_step_kernel(const SurArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint16_t* sW1 = reinterpret_cast<uint16_t*>(smem_raw);  // [kHid][kW1Stride]
   uint16_t* sW2 = sW1 + kHid * kW1Stride;                  // [kHid][kW2Stride]
   uint16_t* sW3 = sW2 + kHid * kW2Stride;                  // [8][kW2Stride]
   float* sB = reinterpret_cast<float*>(sW3 + 8 * kW2Stride);  // b1[128], b2[128], b3[8]
+  float* stage = sB + 2 * kHid + 8;
   {
-    const uint32_t* g = reinterpret_cast<const uint32_t*>(a.wts);
-    uint32_t* s = reinterpret_cast<uint32_t*>(smem_raw);
+    const uint32_t* gw = reinterpret_cast<const uint32_t*>(a.wts);
+    uint32_t* sw = reinterpret_cast<uint32_t*>(smem_raw);
     const int words = (kHid * kW1Stride + kHid * kW2Stride + 8 * kW2Stride) / 2;
-    for (int i = threadIdx.x; i < words; i += blockDim.x) s[i] = g[i];
+    for (int i = threadIdx.x; i < words; i += blockDim.x) sw[i] = gw[i];
     for (int i = threadIdx.x; i < 2 * kHid + 8; i += blockDim.x) sB[i] = a.bias[i];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float* sx = stage + (threadIdx.x >> 5) * kStageFloats;  // [kChunk][kIn]
+  float* sy = sx + kChunk * kIn;                          // [kChunk][4]
+  int* sq = reinterpret_cast<int*>(sy + kChunk * 4);      // [kChunk]
+  const unsigned below = (1u << lane) - 1u;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const int64_t n_tiles = (a.n_slots + 15) / 16;
+  const int64_t n_chunks = (a.n_slots + kChunk - 1) / kChunk;
   unsigned long long fallbacks = 0;
-  for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < n_tiles;
-       tile += warps_total) {
-    const int64_t q0 = tile * 16 + g, q1 = q0 + 8;
-    const SurNode v0 = load_node(a, q0), v1 = load_node(a, q1);
-    const bool fb0 = v0.fiber >= 0 && use_plain_step(a, v0);
-    const bool fb1 = v1.fiber >= 0 && use_plain_step(a, v1);
-    const bool net0 = v0.fiber >= 0 && !fb0, net1 = v1.fiber >= 0 && !fb1;
-    if (__any_sync(0xffffffffu, net0 || net1)) {
-    // normalised features, split into bf16 hi + lo parts (FP32-accurate inputs)
-    float x0[kIn], x1[kIn];
-    {
-      const float r0[kIn] = {v0.u, v0.m, v0.h, v0.n, v0.s};
-      const float r1[kIn] = {v1.u, v1.m, v1.h, v1.n, v1.s};
+  for (int64_t chunk = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); chunk < n_chunks;
+       chunk += warps_total) {
+    const int64_t q = chunk * kChunk + 2 * lane;  // slots q, q + 1 (n_slots is even)
+    float u[2] = {0, 0}, m[2] = {0, 0}, h[2] = {0, 0}, n[2] = {0, 0};
+    int code[2] = {-1, -1};
+    if (q < a.n_slots) {
+      const float2 vu = *reinterpret_cast<const float2*>(a.u + q);
+      const float2 vm = *reinterpret_cast<const float2*>(a.m + q);
+      const float2 vh = *reinterpret_cast<const float2*>(a.h + q);
+      const float2 vn = *reinterpret_cast<const float2*>(a.n + q);
+      u[0] = vu.x; u[1] = vu.y; m[0] = vm.x; m[1] = vm.y;
+      h[0] = vh.x; h[1] = vh.y; n[0] = vn.x; n[1] = vn.y;
+      code[0] = a.slot_code[q];
+      code[1] = a.slot_code[q + 1];
+    }
+    uint32_t smask[2] = {0u, 0u};
+    bool fb[2], net[2];
 #pragma unroll
-      for (int k = 0; k < kIn; ++k) {
-        x0[k] = (r0[k] - a.in_mu[k]) * a.in_inv_sigma[k];
-        x1[k] = (r1[k] - a.in_mu[k]) * a.in_inv_sigma[k];
-      }
+    for (int j = 0; j < 2; ++j) {
+      if (code[j] >= 0 && (code[j] & 1)) smask[j] = a.fiber_stim[code[j] >> 1];
+      const float raw[kIn] = {u[j], m[j], h[j], n[j], (float)__popc(smask[j]) / (float)a.n_sub};
+      const bool plain = use_plain_step(a, raw);
+      fb[j] = code[j] >= 0 && plain;
+      net[j] = code[j] >= 0 && !plain;
     }
-    auto feat = [&](const float (&x)[kIn], int col) -> float {
-      if (col < kIn) return __bfloat162float(__float2bfloat16_rn(x[col]));
-      if (col < 2 * kIn) {
-        const float hi = __bfloat162float(__float2bfloat16_rn(x[col - kIn]));
-        return x[col - kIn] - hi;
+    if (fb[0] || fb[1]) {
+      // the plain HH step on both slots (same arithmetic as the split-step
+      // kernel's reaction); only the slots that take it are stored
+      float uu[2] = {u[0], u[1]}, mm[2] = {m[0], m[1]}, hh[2] = {h[0], h[1]}, nn[2] = {n[0], n[1]};
+      for (int k = 0; k < a.n_sub; ++k) {
+        const uint32_t on = ((smask[0] >> k) & 1u) | (((smask[1] >> k) & 1u) << 1);
+        if (on) heun_nodes<2, true>(uu, mm, hh, nn, a.hh, on);
+        else heun_nodes<2, false>(uu, mm, hh, nn, a.hh, 0u);
       }
-      return 0.0f;
-    };
-    uint32_t A1[4];
-    A1[0] = pack_bf16(feat(x0, 2 * t), feat(x0, 2 * t + 1));
-    A1[1] = pack_bf16(feat(x1, 2 * t), feat(x1, 2 * t + 1));
-    A1[2] = pack_bf16(feat(x0, 2 * t + 8), feat(x0, 2 * t + 9));
-    A1[3] = pack_bf16(feat(x1, 2 * t + 8), feat(x1, 2 * t + 9));
-    // layer 1: 16 n-tiles of 8 neurons, one k-tile
-    uint32_t A2[8][4];
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
-      const uint32_t* w0 = reinterpret_cast<const uint32_t*>(sW1 + (16 * kk + g) * kW1Stride);
-      const uint32_t* w1 = reinterpret_cast<const uint32_t*>(sW1 + (16 * kk + 8 + g) * kW1Stride);
-      mma_bf16(c0, A1, w0[t], w0[t + 4]);
-      mma_bf16(c1, A1, w1[t], w1[t + 4]);
-      to_a_frag(c0, c1, sB + 16 * kk, sB + 16 * kk + 8, t, A2[kk]);
+      for (int j = 0; j < 2; ++j)
+        if (fb[j]) {
+          a.u[q + j] = uu[j];
+          a.m[q + j] = mm[j];
+          a.h[q + j] = hh[j];
+          a.n[q + j] = nn[j];
+          ++fallbacks;
+        }
     }
-    // layer 2: 16 n-tiles, 8 k-tiles
-    uint32_t A3[8][4];
+    // compact the network nodes of the chunk into the staging area
+    const unsigned b0 = __ballot_sync(0xffffffffu, net[0]), b1 = __ballot_sync(0xffffffffu, net[1]);
+    const int count = __popc(b0) + __popc(b1);
+    if (count == 0) continue;  // warp-uniform
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
-      const uint32_t* w0 = reinterpret_cast<const uint32_t*>(sW2 + (16 * kk + g) * kW2Stride);
-      const uint32_t* w1 = reinterpret_cast<const uint32_t*>(sW2 + (16 * kk + 8 + g) * kW2Stride);
+    for (int j = 0; j < 2; ++j) {
+      if (!net[j]) continue;
+      const int r = j == 0 ? __popc(b0 & below) : __popc(b0) + __popc(b1 & below);
+      const float raw[kIn] = {u[j], m[j], h[j], n[j], (float)__popc(smask[j]) / (float)a.n_sub};
 #pragma unroll
-      for (int k2 = 0; k2 < 8; ++k2) {
-        mma_bf16(c0, A2[k2], w0[8 * k2 + t], w0[8 * k2 + t + 4]);
-        mma_bf16(c1, A2[k2], w1[8 * k2 + t], w1[8 * k2 + t + 4]);
-      }
-      to_a_frag(c0, c1, sB + kHid + 16 * kk, sB + kHid + 16 * kk + 8, t, A3[kk]);
+      for (int k = 0; k < kIn; ++k) sx[r * kIn + k] = (raw[k] - a.in_mu[k]) * a.in_inv_sigma[k];
+      sy[r * 4 + 0] = u[j];
+      sy[r * 4 + 1] = m[j];
+      sy[r * 4 + 2] = h[j];
+      sy[r * 4 + 3] = n[j];
+      sq[r] = (int)(q + j);
     }
-    // layer 3: one n-tile (4 outputs padded to 8), 8 k-tiles
-    float o[4] = {0, 0, 0, 0};
-    {
-      const uint32_t* w = reinterpret_cast<const uint32_t*>(sW3 + g * kW2Stride);
-#pragma unroll
-      for (int k2 = 0; k2 < 8; ++k2) mma_bf16(o, A3[k2], w[8 * k2 + t], w[8 * k2 + t + 4]);
-    }
-    // lane t = 0 holds outputs 0, 1 (du, dm) and t = 1 outputs 2, 3 (dh, dn)
-    // of node rows g (o[0], o[1]) and g + 8 (o[2], o[3])
-    if (t < 2) {
-      const int k0 = 2 * t, k1 = 2 * t + 1;
-      const float b0 = sB[2 * kHid + k0], b1 = sB[2 * kHid + k1];
-      float* dst0 = k0 == 0 ? a.u : a.h;
-      float* dst1 = k1 == 1 ? a.m : a.n;
-      if (net0) {
-        const float y0 = k0 == 0 ? v0.u : v0.h, y1 = k1 == 1 ? v0.m : v0.n;
-        dst0[q0] = y0 + fmaf(o[0] + b0, a.out_sigma[k0], a.out_mu[k0]);
-        dst1[q0] = y1 + fmaf(o[1] + b1, a.out_sigma[k1], a.out_mu[k1]);
-      }
-      if (net1) {
-        const float y0 = k0 == 0 ? v1.u : v1.h, y1 = k1 == 1 ? v1.m : v1.n;
-        dst0[q1] = y0 + fmaf(o[2] + b0, a.out_sigma[k0], a.out_mu[k0]);
-        dst1[q1] = y1 + fmaf(o[3] + b1, a.out_sigma[k1], a.out_mu[k1]);
-      }
-    }
-    }  // network part of the tile
-    // fallback: the plain HH reaction step, node row g by lane t = 0 and
-    // node row g + 8 by lane t = 1
-    if ((t == 0 && fb0) || (t == 1 && fb1)) {
-      SurNode v = t == 0 ? v0 : v1;
-      const int64_t q = t == 0 ? q0 : q1;
-      reaction_node(v.u, v.m, v.h, v.n, v.mask, a.n_sub, a.hh);
-      a.u[q] = v.u;
-      a.m[q] = v.m;
-      a.h[q] = v.h;
-      a.n[q] = v.n;
-      ++fallbacks;
-    }
+    __syncwarp();
+    for (int base = 0; base < count; base += 16) network_tile(a, sW1, sW2, sW3, sB, sx, sy, sq, base, count, g, t);
+    __syncwarp();  // the staging area is rewritten by the next chunk
   }
   if (fallbacks) atomicAdd(a.fallback_count, fallbacks);
 }
@@ -460,7 +484,7 @@ __global__ void fiber_stim_kernel(const FiberDesc* fibers, int32_t n_fibers, con
 
 size_t sur_smem_bytes() {
   return 2 * ((size_t)kHid * kW1Stride + (size_t)kHid * kW2Stride + 8 * (size_t)kW2Stride) +
-         4 * (2 * (size_t)kHid + 8);
+         4 * (2 * (size_t)kHid + 8) + 4 * (size_t)kStageFloats * (kSurThreads / 32);
 }
 
 int launch_hh_reaction(const HHConst& c, float vrest, int n_sub, int64_t count, const float* in,
@@ -520,11 +544,12 @@ int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream)
 }
 
 int launch_sur_step(const SurArgs& a, void* stream) {
-  const int64_t tiles = (a.n_slots + 15) / 16;
-  int blocks = (int)((tiles + 3) / 4);
+  const int64_t chunks = (a.n_slots + kChunk - 1) / kChunk;
+  const int64_t warps = kSurThreads / 32;
+  int64_t blocks = (chunks + warps - 1) / warps;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  sur_step_kernel<<<blocks, 128, sur_smem_bytes(), (cudaStream_t)stream>>>(a);
+  sur_step_kernel<<<(int)blocks, kSurThreads, sur_smem_bytes(), (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 

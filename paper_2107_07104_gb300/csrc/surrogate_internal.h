@@ -25,8 +25,7 @@ constexpr int kW2Stride = 136;
 
 struct SurArgs {
   float *u, *m, *h, *n;         // padded state arrays (u = V - Vrest)
-  const FiberDesc* fibers;
-  const int32_t* slot_fiber;    // fiber of each slot (-1: idle lane)
+  const int32_t* slot_code;     // per slot: -1 padding, else (fiber << 1) | (node in its junction's stimulus range)
   const uint8_t* fiber_stim;    // stimulus substep mask of each fiber for this step
   const uint16_t* wts;          // bf16 images W1 | W2 | W3
   const float* bias;            // b1 (128) | b2 (128) | b3 (8)
