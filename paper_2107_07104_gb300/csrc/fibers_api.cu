@@ -71,6 +71,8 @@ struct fib_ctx {
 
   // reaction-step surrogate (FIB_MODE_SURROGATE)
   int32_t* d_slot_fiber = nullptr;   // surrogate: per-slot code (fiber << 1 | stimulated), -1 padding
+  int32_t* d_net_list = nullptr;     // surrogate: slots of the current step's network nodes
+  unsigned int* d_net_count = nullptr;  // surrogate: their number
   uint8_t* d_fiber_stim = nullptr;   // per-fiber stimulus substep mask of the current step
   uint16_t* d_sur_wts = nullptr;     // bf16 weight images
   float* d_sur_bias = nullptr;
@@ -228,6 +230,8 @@ void free_layout(fib_ctx* c) {
   dfree(c->d_rows);
   dfree(c->d_recs);
   dfree(c->d_slot_fiber);
+  dfree(c->d_net_list);
+  dfree(c->d_net_count);
 }
 
 // Builds the padded layout, CTA packing and solver tables for tuning t.
@@ -331,6 +335,8 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   CU(c, cudaMalloc(&c->d_rows, es * tab.rows.size()));
   CU(c, cudaMalloc(&c->d_recs, es * std::max<size_t>(tab.recs.size(), 1)));
   if (!fd.empty()) CU(c, cudaMemcpy(c->d_fibers, fd.data(), sizeof(FiberDesc) * fd.size(), cudaMemcpyHostToDevice));
+  if (c->p.mode == FIB_MODE_SURROGATE && slot > INT32_MAX)
+    return fail(c, FIB_EINVAL, "surrogate mode holds slot indices in 32 bits: %lld slots", (long long)slot);
   if (c->p.mode == FIB_MODE_SURROGATE && slot > 0) {
     // per-slot code for the surrogate kernel: -1 padding, else
     // (fiber << 1) | (node within the junction's stimulus range)
@@ -343,6 +349,9 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
     }
     CU(c, cudaMalloc(&c->d_slot_fiber, sizeof(int32_t) * sf.size()));
     CU(c, cudaMemcpy(c->d_slot_fiber, sf.data(), sizeof(int32_t) * sf.size(), cudaMemcpyHostToDevice));
+    CU(c, cudaMalloc(&c->d_net_list, sizeof(int32_t) * sf.size()));
+    CU(c, cudaMalloc(&c->d_net_count, sizeof(unsigned int)));
+    CU(c, cudaMemset(c->d_net_count, 0, sizeof(unsigned int)));
   }
   if (!wm.empty()) CU(c, cudaMemcpy(c->d_warps, wm.data(), sizeof(WarpMap) * wm.size(), cudaMemcpyHostToDevice));
   if (fp64) {
@@ -554,6 +563,8 @@ fib_status surrogate_steps(fib_ctx* c, int64_t n) {
   s.wts = c->d_sur_wts;
   s.bias = c->d_sur_bias;
   s.fallback_count = c->d_fallback;
+  s.net_list = c->d_net_list;
+  s.net_count = c->d_net_count;
   s.n_slots = c->slots_total;
   s.hh = a.hh;
   for (int k = 0; k < kIn; ++k) {
@@ -569,6 +580,7 @@ fib_status surrogate_steps(fib_ctx* c, int64_t n) {
     s.out_sigma[k] = c->out_sigma[k];
   }
   s.n_sub = (int32_t)c->n_sub;
+  s.inv_n_sub = 1.0f / (float)c->n_sub;
   s.hw = c->p.stim_half_width;
   a.phases = 1;
   fib_status st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, c->stream), "diffusion");
@@ -576,7 +588,7 @@ fib_status surrogate_steps(fib_ctx* c, int64_t n) {
   ++c->launches;
   for (int64_t i = 0; i < n; ++i) {
     st = check_launch(c, launch_fiber_stim(c->d_fibers, c->n_fibers, c->d_mu_off, c->d_fire_k, c->n_mu, c->d_step, i,
-                                           (int)c->n_sub, (int)c->pulse, c->d_fiber_stim, c->stream),
+                                           (int)c->n_sub, (int)c->pulse, c->d_fiber_stim, c->d_net_count, c->stream),
                       "stimulus");
     if (st != FIB_OK) return st;
     st = check_launch(c, launch_sur_step(s, c->stream), "surrogate");

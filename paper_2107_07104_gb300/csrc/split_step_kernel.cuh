@@ -380,16 +380,21 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   s_coef[kPKDn * kStride + tid] = p > 0 ? sc.rec[6 - a.rec_stride] : (R)0;
   sc.cf = s_coef + tid;  // own column: read back only by this thread
 
-  // load this thread's K nodes (vectorised: slot and K are multiples of 4)
+  // load this thread's K nodes (vectorised: slot and K are multiples of 4);
+  // a launch without the reaction phase (diffusion only) touches u alone
+  const bool gates = ADAPT || (a.phases & 2) != 0;
   float u[K], m[K], h[K], n[K];
   const int64_t base = fd.slot + (int64_t)p * K;
 #pragma unroll
   for (int j = 0; j < K; j += 4) {
     const float4 vu = *reinterpret_cast<const float4*>(a.u + base + j);
-    const float4 vm = *reinterpret_cast<const float4*>(a.m + base + j);
-    const float4 vh = *reinterpret_cast<const float4*>(a.h + base + j);
-    const float4 vn = *reinterpret_cast<const float4*>(a.n + base + j);
     u[j] = vu.x; u[j + 1] = vu.y; u[j + 2] = vu.z; u[j + 3] = vu.w;
+    float4 vm = make_float4(0.f, 0.f, 0.f, 0.f), vh = vm, vn = vm;
+    if (gates) {
+      vm = *reinterpret_cast<const float4*>(a.m + base + j);
+      vh = *reinterpret_cast<const float4*>(a.h + base + j);
+      vn = *reinterpret_cast<const float4*>(a.n + base + j);
+    }
     m[j] = vm.x; m[j + 1] = vm.y; m[j + 2] = vm.z; m[j + 3] = vm.w;
     h[j] = vh.x; h[j + 1] = vh.y; h[j + 2] = vh.z; h[j + 3] = vh.w;
     n[j] = vn.x; n[j + 1] = vn.y; n[j + 2] = vn.z; n[j + 3] = vn.w;
@@ -514,9 +519,11 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
 #pragma unroll
   for (int j = 0; j < K; j += 4) {
     *reinterpret_cast<float4*>(a.u + base + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
-    *reinterpret_cast<float4*>(a.m + base + j) = make_float4(m[j], m[j + 1], m[j + 2], m[j + 3]);
-    *reinterpret_cast<float4*>(a.h + base + j) = make_float4(h[j], h[j + 1], h[j + 2], h[j + 3]);
-    *reinterpret_cast<float4*>(a.n + base + j) = make_float4(n[j], n[j + 1], n[j + 2], n[j + 3]);
+    if (gates) {
+      *reinterpret_cast<float4*>(a.m + base + j) = make_float4(m[j], m[j + 1], m[j + 2], m[j + 3]);
+      *reinterpret_cast<float4*>(a.h + base + j) = make_float4(h[j], h[j + 1], h[j + 2], h[j + 3]);
+      *reinterpret_cast<float4*>(a.n + base + j) = make_float4(n[j], n[j + 1], n[j + 2], n[j + 3]);
+    }
   }
 }
 

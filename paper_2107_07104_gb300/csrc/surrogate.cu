@@ -7,10 +7,10 @@
 //   * training kernels (FP32 master weights, optional bfloat16 rounding of
 //     weights and activations in the forward pass, straight-through
 //     gradients) and an Adam update;
-//   * sur_step_kernel: inference on BF16 tensor cores (mma.sync m16n8k16,
-//     FP32 accumulation) on the nodes that need it, compacted per warp into
-//     full tiles, with an envelope test that sends nodes outside the
-//     training data's range (or near rest) to the plain HH step.
+//   * the surrogate step: sur_fallback_kernel applies the plain HH step to
+//     nodes outside the training data's range or near rest and lists the
+//     others; sur_net_kernel evaluates the listed nodes on BF16 tensor cores
+//     (mma.sync m16n8k16, FP32 accumulation) in full tiles of 16.
 // Network: x (5) -> 128 -> SiLU -> 128 -> SiLU -> 4, predicting the change of
 // (u, m, h, n) over one split step in normalised units.
 #include <cuda_bf16.h>
@@ -20,6 +20,7 @@
 
 #include "fibers_internal.h"
 #include "hh_device.cuh"
+#include "split_step_kernel.cuh"
 #include "surrogate_internal.h"
 
 namespace fib {
@@ -282,11 +283,17 @@ __device__ __forceinline__ bool use_plain_step(const SurArgs& a, const float (&r
   return outside || quiet;
 }
 
-// Per-warp staging of the nodes that go through the network: normalised
-// features, the state before the step, and the slot.
-constexpr int kChunk = 64;  // slots per warp and iteration: two adjacent slots per lane
-constexpr int kStageFloats = kChunk * (kIn + 4 + 1);
+// Per-warp staging of one tile of network nodes: normalised features, the
+// state before the step, and the slot.
+constexpr int kTileRows = 16;
+constexpr int kStageFloats = kTileRows * (kIn + 4 + 1);
 constexpr int kSurThreads = 128;
+// The plain-step pass takes two adjacent slots per lane (one fiber: fiber
+// slots are 4-aligned), 64 per warp; few registers, so many warps hide the
+// latency of the step's state loads.
+constexpr int kFbNodes = 2;
+constexpr int kFbChunk = 32 * kFbNodes;
+constexpr int kFbThreads = 256;
 
 // Inference tile: rows g and g + 8 of 16 staged nodes starting at `base`.
 __device__ __forceinline__ void network_tile(const SurArgs& a, const uint16_t* sW1, const uint16_t* sW2,
@@ -358,18 +365,110 @@ __device__ __forceinline__ void network_tile(const SurArgs& a, const uint16_t* s
   }
 }
 
-// One reaction step of every slot.  A warp takes 64 consecutive slots, two
-// adjacent ones per lane (same fiber: fiber slots are 4-aligned).  Nodes for
-// the plain step integrate in place, two per lane; nodes for the network are
-// compacted into the warp's staging area and evaluated 16 at a time on the
-// tensor cores, so every tile is full except the last one of a chunk.
-__global__ void __launch_bounds__(kSurThreads) sur_step_kernel(const SurArgs a) {
+// Reaction pass of the surrogate step over every slot.  Nodes outside the
+// network's envelope or near rest take the plain HH step here (the packed
+// Heun code of the split-step kernel, so the same bits as the plain path);
+// the slots of the other nodes are appended to a list for sur_net_kernel,
+// which reads their untouched state.  Node results do not depend on the
+// list's order.
+__global__ void __launch_bounds__(kFbThreads, 4) sur_fallback_kernel(const SurArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t n_chunks = (a.n_slots + kFbChunk - 1) / kFbChunk;
+  unsigned long long fallbacks = 0;
+  for (int64_t chunk = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); chunk < n_chunks;
+       chunk += warps_total) {
+    const int64_t q = chunk * kFbChunk + kFbNodes * lane;  // n_slots is a multiple of 4
+    float u[kFbNodes] = {0, 0}, m[kFbNodes] = {0, 0}, h[kFbNodes] = {0, 0}, n[kFbNodes] = {0, 0};
+    int code[kFbNodes] = {-1, -1};
+    if (q < a.n_slots) {
+      const float2 vu = *reinterpret_cast<const float2*>(a.u + q);
+      const float2 vm = *reinterpret_cast<const float2*>(a.m + q);
+      const float2 vh = *reinterpret_cast<const float2*>(a.h + q);
+      const float2 vn = *reinterpret_cast<const float2*>(a.n + q);
+      const int2 vc = *reinterpret_cast<const int2*>(a.slot_code + q);
+      u[0] = vu.x; u[1] = vu.y; m[0] = vm.x; m[1] = vm.y;
+      h[0] = vh.x; h[1] = vh.y; n[0] = vn.x; n[1] = vn.y;
+      code[0] = vc.x; code[1] = vc.y;
+    }
+    // the two slots share one fiber: its stimulus mask for the step, and
+    // which of them lie in the junction's stimulus range
+    uint32_t jmask = 0, fmask = 0;
+    int fiber = -1;
+#pragma unroll
+    for (int j = 0; j < kFbNodes; ++j)
+      if (code[j] >= 0) {
+        fiber = code[j] >> 1;
+        jmask |= (uint32_t)(code[j] & 1) << j;
+      }
+    if (jmask) fmask = a.fiber_stim[fiber];
+    const float sfrac = (float)__popc(fmask) * a.inv_n_sub;
+    uint32_t fbm = 0, netm = 0;
+#pragma unroll
+    for (int j = 0; j < kFbNodes; ++j) {
+      if (code[j] < 0) continue;
+      const float raw[kIn] = {u[j], m[j], h[j], n[j], ((jmask >> j) & 1u) ? sfrac : 0.0f};
+      if (use_plain_step(a, raw)) fbm |= 1u << j;
+      else netm |= 1u << j;
+    }
+    if (fbm) {
+      float uu[kFbNodes] = {u[0], u[1]}, mm[kFbNodes] = {m[0], m[1]};
+      float hh[kFbNodes] = {h[0], h[1]}, nn[kFbNodes] = {n[0], n[1]};
+      for (int k = 0; k < a.n_sub; ++k) {
+        if (jmask && ((fmask >> k) & 1u)) heun_nodes_packed<kFbNodes, true, false>(uu, mm, hh, nn, a.hh, jmask);
+        else heun_nodes_packed<kFbNodes, false, false>(uu, mm, hh, nn, a.hh, 0u);
+      }
+      if (fbm == 0x3u) {
+        *reinterpret_cast<float2*>(a.u + q) = make_float2(uu[0], uu[1]);
+        *reinterpret_cast<float2*>(a.m + q) = make_float2(mm[0], mm[1]);
+        *reinterpret_cast<float2*>(a.h + q) = make_float2(hh[0], hh[1]);
+        *reinterpret_cast<float2*>(a.n + q) = make_float2(nn[0], nn[1]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kFbNodes; ++j)
+          if ((fbm >> j) & 1u) {
+            a.u[q + j] = uu[j];
+            a.m[q + j] = mm[j];
+            a.h[q + j] = hh[j];
+            a.n[q + j] = nn[j];
+          }
+      }
+      fallbacks += __popc(fbm);
+    }
+    // append the network nodes: one atomic per warp
+    const int cnt = __popc(netm);
+    if (__any_sync(0xffffffffu, cnt > 0)) {
+      int incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      unsigned int base = 0;
+      if (lane == 31) base = atomicAdd(a.net_count, (unsigned int)incl);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      unsigned int pos = base + (unsigned int)(incl - cnt);
+#pragma unroll
+      for (int j = 0; j < kFbNodes; ++j)
+        if ((netm >> j) & 1u) a.net_list[pos++] = (int32_t)(q + j);
+    }
+  }
+  // one atomic per warp: same-address atomics from every thread serialise
+  const unsigned int wsum = __reduce_add_sync(0xffffffffu, (unsigned int)fallbacks);
+  if (lane == 0 && wsum) atomicAdd(a.fallback_count, (unsigned long long)wsum);
+}
+
+// Network pass: the listed nodes in tiles of 16 on the tensor cores.  Each
+// warp stages one tile's inputs in shared memory, then evaluates it.
+__global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint16_t* sW1 = reinterpret_cast<uint16_t*>(smem_raw);  // [kHid][kW1Stride]
   uint16_t* sW2 = sW1 + kHid * kW1Stride;                  // [kHid][kW2Stride]
   uint16_t* sW3 = sW2 + kHid * kW2Stride;                  // [8][kW2Stride]
   float* sB = reinterpret_cast<float*>(sW3 + 8 * kW2Stride);  // b1[128], b2[128], b3[8]
   float* stage = sB + 2 * kHid + 8;
+  const int64_t count = *a.net_count;
+  if (count == 0) return;
   {
     const uint32_t* gw = reinterpret_cast<const uint32_t*>(a.wts);
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem_raw);
@@ -379,85 +478,37 @@ __global__ void __launch_bounds__(kSurThreads) sur_step_kernel(const SurArgs a) 
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float* sx = stage + (threadIdx.x >> 5) * kStageFloats;  // [kChunk][kIn]
-  float* sy = sx + kChunk * kIn;                          // [kChunk][4]
-  int* sq = reinterpret_cast<int*>(sy + kChunk * 4);      // [kChunk]
-  const unsigned below = (1u << lane) - 1u;
-  const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const int64_t n_chunks = (a.n_slots + kChunk - 1) / kChunk;
-  unsigned long long fallbacks = 0;
-  for (int64_t chunk = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); chunk < n_chunks;
-       chunk += warps_total) {
-    const int64_t q = chunk * kChunk + 2 * lane;  // slots q, q + 1 (n_slots is even)
-    float u[2] = {0, 0}, m[2] = {0, 0}, h[2] = {0, 0}, n[2] = {0, 0};
-    int code[2] = {-1, -1};
-    if (q < a.n_slots) {
-      const float2 vu = *reinterpret_cast<const float2*>(a.u + q);
-      const float2 vm = *reinterpret_cast<const float2*>(a.m + q);
-      const float2 vh = *reinterpret_cast<const float2*>(a.h + q);
-      const float2 vn = *reinterpret_cast<const float2*>(a.n + q);
-      u[0] = vu.x; u[1] = vu.y; m[0] = vm.x; m[1] = vm.y;
-      h[0] = vh.x; h[1] = vh.y; n[0] = vn.x; n[1] = vn.y;
-      code[0] = a.slot_code[q];
-      code[1] = a.slot_code[q + 1];
-    }
-    uint32_t smask[2] = {0u, 0u};
-    bool fb[2], net[2];
+  float* sx = stage + (threadIdx.x >> 5) * kStageFloats;  // [kTileRows][kIn]
+  float* sy = sx + kTileRows * kIn;                       // [kTileRows][4]
+  int* sq = reinterpret_cast<int*>(sy + kTileRows * 4);   // [kTileRows]
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t n_tiles = (count + kTileRows - 1) / kTileRows;
+  for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < n_tiles;
+       tile += warps_total) {
+    const int64_t e0 = tile * kTileRows;
+    const int rows = (int)(count - e0 < kTileRows ? count - e0 : kTileRows);
+    if (lane < rows) {
+      const int64_t q = a.net_list[e0 + lane];
+      const int code = a.slot_code[q];
+      const uint32_t fmask = (code & 1) ? a.fiber_stim[code >> 1] : 0u;
+      const float raw[kIn] = {a.u[q], a.m[q], a.h[q], a.n[q], (float)__popc(fmask) * a.inv_n_sub};
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (code[j] >= 0 && (code[j] & 1)) smask[j] = a.fiber_stim[code[j] >> 1];
-      const float raw[kIn] = {u[j], m[j], h[j], n[j], (float)__popc(smask[j]) / (float)a.n_sub};
-      const bool plain = use_plain_step(a, raw);
-      fb[j] = code[j] >= 0 && plain;
-      net[j] = code[j] >= 0 && !plain;
-    }
-    if (fb[0] || fb[1]) {
-      // the plain HH step on both slots (same arithmetic as the split-step
-      // kernel's reaction); only the slots that take it are stored
-      float uu[2] = {u[0], u[1]}, mm[2] = {m[0], m[1]}, hh[2] = {h[0], h[1]}, nn[2] = {n[0], n[1]};
-      for (int k = 0; k < a.n_sub; ++k) {
-        const uint32_t on = ((smask[0] >> k) & 1u) | (((smask[1] >> k) & 1u) << 1);
-        if (on) heun_nodes<2, true>(uu, mm, hh, nn, a.hh, on);
-        else heun_nodes<2, false>(uu, mm, hh, nn, a.hh, 0u);
-      }
+      for (int k = 0; k < kIn; ++k) sx[lane * kIn + k] = (raw[k] - a.in_mu[k]) * a.in_inv_sigma[k];
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (fb[j]) {
-          a.u[q + j] = uu[j];
-          a.m[q + j] = mm[j];
-          a.h[q + j] = hh[j];
-          a.n[q + j] = nn[j];
-          ++fallbacks;
-        }
-    }
-    // compact the network nodes of the chunk into the staging area
-    const unsigned b0 = __ballot_sync(0xffffffffu, net[0]), b1 = __ballot_sync(0xffffffffu, net[1]);
-    const int count = __popc(b0) + __popc(b1);
-    if (count == 0) continue;  // warp-uniform
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (!net[j]) continue;
-      const int r = j == 0 ? __popc(b0 & below) : __popc(b0) + __popc(b1 & below);
-      const float raw[kIn] = {u[j], m[j], h[j], n[j], (float)__popc(smask[j]) / (float)a.n_sub};
-#pragma unroll
-      for (int k = 0; k < kIn; ++k) sx[r * kIn + k] = (raw[k] - a.in_mu[k]) * a.in_inv_sigma[k];
-      sy[r * 4 + 0] = u[j];
-      sy[r * 4 + 1] = m[j];
-      sy[r * 4 + 2] = h[j];
-      sy[r * 4 + 3] = n[j];
-      sq[r] = (int)(q + j);
+      for (int k = 0; k < 4; ++k) sy[lane * 4 + k] = raw[k];
+      sq[lane] = (int)q;
     }
     __syncwarp();
-    for (int base = 0; base < count; base += 16) network_tile(a, sW1, sW2, sW3, sB, sx, sy, sq, base, count, g, t);
-    __syncwarp();  // the staging area is rewritten by the next chunk
+    network_tile(a, sW1, sW2, sW3, sB, sx, sy, sq, 0, rows, g, t);
+    __syncwarp();  // the staging area is rewritten by the next tile
   }
-  if (fallbacks) atomicAdd(a.fallback_count, fallbacks);
 }
 
 // Stimulus substep mask of every fiber for one split step.
 __global__ void fiber_stim_kernel(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off,
                                   const int64_t* fire_k, int32_t n_mu, const int64_t* step_base, int64_t step_offset,
-                                  int n_sub, int pulse, uint8_t* out) {
+                                  int n_sub, int pulse, uint8_t* out, unsigned int* net_count) {
+  if (net_count && blockIdx.x == 0 && threadIdx.x == 0) *net_count = 0;  // the step's network list starts empty
   for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < n_fibers; f += gridDim.x * blockDim.x) {
     const int mu = fibers[f].mu;
     uint8_t mask = 0;
@@ -544,26 +595,30 @@ int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream)
 }
 
 int launch_sur_step(const SurArgs& a, void* stream) {
-  const int64_t chunks = (a.n_slots + kChunk - 1) / kChunk;
-  const int64_t warps = kSurThreads / 32;
+  const int64_t chunks = (a.n_slots + kFbChunk - 1) / kFbChunk;
+  const int64_t warps = kFbThreads / 32;
   int64_t blocks = (chunks + warps - 1) / warps;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  sur_step_kernel<<<(int)blocks, kSurThreads, sur_smem_bytes(), (cudaStream_t)stream>>>(a);
+  sur_fallback_kernel<<<(int)blocks, kFbThreads, 0, (cudaStream_t)stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return (int)e;
+  // the list's length is known on the device only: a fixed grid strides over it
+  sur_net_kernel<<<152 * 4, kSurThreads, sur_smem_bytes(), (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
 int launch_fiber_stim(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off, const int64_t* fire_k,
                       int32_t n_mu, const int64_t* step_base, int64_t step_offset, int n_sub, int pulse, uint8_t* out,
-                      void* stream) {
-  if (n_fibers <= 0) return 0;
-  fiber_stim_kernel<<<(n_fibers + 255) / 256, 256, 0, (cudaStream_t)stream>>>(fibers, n_fibers, mu_off, fire_k, n_mu,
-                                                                             step_base, step_offset, n_sub, pulse, out);
+                      unsigned int* net_count, void* stream) {
+  const int blocks = n_fibers > 0 ? (n_fibers + 255) / 256 : 1;
+  fiber_stim_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(fibers, n_fibers, mu_off, fire_k, n_mu, step_base,
+                                                             step_offset, n_sub, pulse, out, net_count);
   return (int)cudaGetLastError();
 }
 
 int sur_set_smem_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(sur_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(sur_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sur_smem_bytes());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);

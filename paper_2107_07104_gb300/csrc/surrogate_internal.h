@@ -30,6 +30,8 @@ struct SurArgs {
   const uint16_t* wts;          // bf16 images W1 | W2 | W3
   const float* bias;            // b1 (128) | b2 (128) | b3 (8)
   unsigned long long* fallback_count;
+  int32_t* net_list;            // slots of the step's network nodes (capacity n_slots)
+  unsigned int* net_count;      // their number (reset by the step's stimulus kernel)
   int64_t n_slots;
   HHConst hh;
   float in_mu[kIn], in_inv_sigma[kIn];
@@ -37,6 +39,7 @@ struct SurArgs {
   float env_lo[kIn], env_hi[kIn];      // training envelope: outside -> plain HH
   float quiet_lo[kIn], quiet_hi[kIn];  // neighbourhood of rest: inside -> plain HH
   int32_t n_sub, hw;
+  float inv_n_sub;              // 1 / n_sub (stimulus fraction of a split step)
 };
 
 size_t sur_smem_bytes();
@@ -52,6 +55,6 @@ int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream)
 int launch_sur_step(const SurArgs& a, void* stream);
 int launch_fiber_stim(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off, const int64_t* fire_k,
                       int32_t n_mu, const int64_t* step_base, int64_t step_offset, int n_sub, int pulse, uint8_t* out,
-                      void* stream);
+                      unsigned int* net_count, void* stream);
 
 }  // namespace fib
