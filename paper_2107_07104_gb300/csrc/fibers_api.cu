@@ -85,6 +85,9 @@ struct fib_ctx {
   std::string err;
 };
 
+// Surrogate mode's split steps (defined below), enqueued on stream s.
+fib_status surrogate_steps(fib_ctx* c, cudaStream_t s, int64_t n);
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -469,11 +472,14 @@ fib_status enqueue_launches(fib_ctx* c, cudaStream_t s, int64_t offset0, int64_t
   return FIB_OK;
 }
 
+// Captures graph_steps split steps (and the step counter's advance) of the
+// context's mode into one CUDA graph.
 fib_status build_graph(fib_ctx* c) {
   const int64_t G = c->tune.graph_steps;
   CU(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   const int64_t before = c->launches;
-  fib_status st = enqueue_launches(c, c->cap_stream, 0, G);
+  fib_status st = c->p.mode == FIB_MODE_SURROGATE ? surrogate_steps(c, c->cap_stream, G)
+                                                  : enqueue_launches(c, c->cap_stream, 0, G);
   int e = st == FIB_OK ? launch_advance(c->d_step, G, c->cap_stream) : 0;
   cudaGraph_t g = nullptr;
   cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
@@ -547,7 +553,7 @@ fib_status scatter_state(fib_ctx* c, const float* src) {
 
 // Surrogate mode: diffusion halves by the step kernel (reaction phase off),
 // the reaction step by the tensor-core surrogate with per-node HH fallback.
-fib_status surrogate_steps(fib_ctx* c, int64_t n) {
+fib_status surrogate_steps(fib_ctx* c, cudaStream_t stream, int64_t n) {
   if (c->n_ctas == 0) return FIB_OK;
   StepArgs a = make_args(c);
   a.n_steps = 1;
@@ -583,18 +589,18 @@ fib_status surrogate_steps(fib_ctx* c, int64_t n) {
   s.inv_n_sub = 1.0f / (float)c->n_sub;
   s.hw = c->p.stim_half_width;
   a.phases = 1;
-  fib_status st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, c->stream), "diffusion");
+  fib_status st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, stream), "diffusion");
   if (st != FIB_OK) return st;
   ++c->launches;
   for (int64_t i = 0; i < n; ++i) {
     st = check_launch(c, launch_fiber_stim(c->d_fibers, c->n_fibers, c->d_mu_off, c->d_fire_k, c->n_mu, c->d_step, i,
-                                           (int)c->n_sub, (int)c->pulse, c->d_fiber_stim, c->d_net_count, c->stream),
+                                           (int)c->n_sub, (int)c->pulse, c->d_fiber_stim, c->d_net_count, stream),
                       "stimulus");
     if (st != FIB_OK) return st;
-    st = check_launch(c, launch_sur_step(s, c->stream), "surrogate");
+    st = check_launch(c, launch_sur_step(s, stream), "surrogate");
     if (st != FIB_OK) return st;
     a.phases = (i + 1 < n) ? (4 | 1) : 4;
-    st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, c->stream), "diffusion");
+    st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, stream), "diffusion");
     if (st != FIB_OK) return st;
     c->launches += 3;
   }
@@ -766,16 +772,8 @@ fib_status step(fib_ctx* c, int64_t n_steps) {
   if (n_steps < 0) return fail(c, FIB_EINVAL, "n_steps < 0");
   if (n_steps == 0) return FIB_OK;
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
-  if (c->p.mode == FIB_MODE_SURROGATE) {
-    if (!c->sur_loaded) return fail(c, FIB_ESTATE, "surrogate mode needs fibers_load_surrogate before step");
-    fib_status st = surrogate_steps(c, n_steps);
-    if (st != FIB_OK) return st;
-    st = check_launch(c, launch_advance(c->d_step, n_steps, c->stream), "advance");
-    if (st != FIB_OK) return st;
-    ++c->launches;
-    c->next_step += n_steps;
-    return FIB_OK;
-  }
+  const bool sur = c->p.mode == FIB_MODE_SURROGATE;
+  if (sur && !c->sur_loaded) return fail(c, FIB_ESTATE, "surrogate mode needs fibers_load_surrogate before step");
   const int64_t G = c->tune.graph_steps;
   if (G > 0 && n_steps >= G && c->n_ctas > 0) {
     if (!c->graph) {
@@ -790,7 +788,7 @@ fib_status step(fib_ctx* c, int64_t n_steps) {
     }
   }
   if (n_steps > 0) {
-    fib_status st = enqueue_launches(c, c->stream, 0, n_steps);
+    fib_status st = sur ? surrogate_steps(c, c->stream, n_steps) : enqueue_launches(c, c->stream, 0, n_steps);
     if (st != FIB_OK) return st;
     st = check_launch(c, launch_advance(c->d_step, n_steps, c->stream), "advance");
     if (st != FIB_OK) return st;
@@ -1086,6 +1084,8 @@ fib_status fibers_load_surrogate(fib_ctx* c, const float* blob, size_t n_floats)
   CU(c, cudaMemcpy(c->d_sur_bias, bias.data(), sizeof(float) * bias.size(), cudaMemcpyHostToDevice));
   CU(c, (cudaError_t)sur_set_smem_attributes());
   c->sur_loaded = true;
+  if (c->graph) cudaGraphExecDestroy(c->graph);  // captured normalisation and envelope changed
+  c->graph = nullptr;
   return FIB_OK;
 }
 

@@ -168,3 +168,26 @@ def test_surrogate_on_held_out_bundle(trained_blob):
     assert (np.isnan(to) & ~np.isnan(ts)).sum() <= 0.01 * fired.sum()  # no spurious excitation
     assert act <= 0.05                                # activation times within 0.05 ms
     assert es[1] <= 0.01                              # trajectory relative L2 (max|dV| is reported, not bounded)
+
+
+def test_surrogate_mode_graphs_match_eager_launches():
+    """Surrogate split steps replayed as CUDA graphs give the same bits as
+    launched one by one, with the committed network handling the firing
+    nodes; reloading the weights rebuilds the graph."""
+    w = W.small_ragged(seed=33, n_fibers=40, lo=300, hi=1200, n_steps=600)
+    w.mu_offsets = np.arange(5, dtype=np.int64)           # one firing per motor unit
+    w.fire_times = np.array([0.05, 0.3, 0.6, 0.9])
+    blob = S.load_blob()
+    out = []
+    for graph_steps in (0, 200, 200):
+        with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE, tuning=dict(graph_steps=graph_steps)) as f:
+            F.fibers_load_surrogate(f.ctx, blob)
+            f.step(400)
+            if len(out) == 2:
+                F.fibers_load_surrogate(f.ctx, blob)  # invalidates the captured graph
+            f.step(200)
+            _, fb = f.stats()
+            out.append((f.read_state(), fb))
+    assert out[0][1] < 600 * w.total_nodes  # the network did handle nodes
+    for st, fb in out[1:]:
+        assert np.array_equal(st, out[0][0]) and fb == out[0][1]
