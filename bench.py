@@ -39,7 +39,7 @@ from paper_2107_07104_gb300 import workloads as W  # noqa: E402
 METRIC = "fiber node-updates/s (full split step) at max|ΔVm|≤0.5 mV, plain FP32 vs surrogate"
 UNIT = "node-updates/s"
 WORKLOAD = "bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz"
-# Algorithmic work per node-update of the plain FP32 path:
+# Algorithmic work per node-update of the plain FP32 path (the method's operation counts):
 BYTES_PER_NODE_UPDATE = 32.0     # read + write V, m, h, n (FP32) once per split step
 FMA_OPS_PER_NODE_UPDATE = 238.0  # FP32 FMA-pipe operations of the method per split step
 EX2_OPS_PER_NODE_UPDATE = 24.0   # 2^x special-function operations per split step (4 per HH RHS)
@@ -213,7 +213,22 @@ def oracle_rate(w, fibers: int, steps: int):
     oracle.run(sub.params, sub.n_nodes, sub.mu_of_fiber, sub.junction, sub.mu_offsets, sub.fire_times, state, 0,
                steps, n_threads=cores)
     dt = time.perf_counter() - t0
+    oracle_rate.last = (sub, state[:sub.total_nodes].copy())
     return sub.total_nodes * steps / dt, dt, cores, sub.total_nodes
+
+
+def accuracy_vs_oracle(tune, steps):
+    """The GPU path on the CPU-baseline sample (same fibers, same steps, the
+    bench's launch shape) against the FP64 oracle's final V."""
+    from paper_2107_07104_gb300 import fibers as F
+    sub, v_ref = oracle_rate.last
+    with F.Fibers.from_workload(sub, tuning=tune) as f:
+        f.step(steps)
+        v = f.read_vm().astype(np.float64)
+    d = v - v_ref
+    return {"fibers": int(sub.n_fibers), "split_steps": int(steps), "max_abs_mv": float(np.max(np.abs(d))),
+            "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(v_ref)), "tolerance_mv": 0.5,
+            "depolarised_nodes": int(np.sum(v_ref > v_ref.min() + 10.0))}
 
 
 def run_reference(args, world, rank):
@@ -337,6 +352,9 @@ def run_gpu(args, world, rank, local, dist):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_fibers} of 7744 fibers x 1481 nodes, {args.cpu_steps} split steps "
                          f"({dt:.1f} s of FP64 oracle on {cores} threads)"}
+        accuracy = accuracy_vs_oracle(tune, args.cpu_steps)
+    else:
+        accuracy = None
     clocks = clk.summary()
     sur = None if args.no_surrogate else surrogate_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     adaptive = None if args.no_adaptive else adaptive_leg(args, w, tune, stream, dev, total, per_gpu_rate)
@@ -363,6 +381,7 @@ def run_gpu(args, world, rank, local, dist):
                                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         },
         "cpu_baseline": cpu,
+        "accuracy_vs_oracle": accuracy,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,
                 "includes": "fibers_create + set_stimulus_times from host arrays, step(K), read_vm to host"},
@@ -415,7 +434,13 @@ def surrogate_leg(args, w, tune, stream, dev, total, plain_rate):
     rate = float(total) * args.steps / (ms / 1e3)
     sub = firing_subset(w)
     acc = agreement(trajectory(sub), trajectory(sub, mode=F.FIB_MODE_SURROGATE, blob=blob), sub)
+    # per node and split step the reaction pass reads u, m, h, n and the slot
+    # code and writes u, m, h, n; the diffusion-only launch reads and writes u
+    sur_bytes = 44.0
+    hbm_peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
     return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
+            "hbm": {"bytes_per_node_update": sur_bytes, "achieved_gbs": rate * sur_bytes / 1e9, "peak_gbs": hbm_peak,
+                    "frac": rate * sur_bytes / 1e9 / hbm_peak},
             "network_fraction_of_node_updates": 1.0 - (fb1 - fb0) / (float(total) * args.steps),
             "accuracy_vs_plain_fp32": acc,
             "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}

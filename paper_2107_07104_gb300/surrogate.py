@@ -7,7 +7,7 @@ become samples, shuffles batches, and assembles the blob that
 fibers_load_surrogate reads.  Torch provides device memory and index
 gathers.
 
-Samples (SURVEY row a8): node states (u, m, h, n) read from trajectories of
+Samples: node states (u, m, h, n) read from trajectories of
 the plain FP32 method on seeded bundles, plus the stimulus pattern of the
 step; the target is the change of the state over the reaction part of one
 split step, computed by the plain HH step.  Nodes away from rest are
