@@ -54,7 +54,7 @@ typedef enum {
   FIB_ENONFINITE = 4,  /* the state became NaN/Inf; it stays readable */
   FIB_ETIMEOUT = 5,    /* a bounded host wait gave up */
   FIB_ESTATE = 6,      /* call not valid in the current state */
-  FIB_ENOTSUP = 7      /* valid request that this build does not support */
+  FIB_ENOTSUP = 7      /* valid request that the library does not support */
 } fib_status;
 
 /* Solve modes. */
