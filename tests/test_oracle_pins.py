@@ -408,6 +408,33 @@ def test_second_order_scheme_at_8x_the_step_beats_godunov_implicit_euler():
     assert e_g < 2.0, e_g  # and both are close to the reference
 
 
+@pytest.mark.slow
+def test_dt_ratio_study_balances_0d_and_1d_errors():
+    """The thesis's ratio K = dt_1D / dt_0D (sec. on numerical improvements):
+    refining the 0D substeps helps only until the 0D error drops below the
+    splitting and 1D errors -- about K = 5 for Strang and K = 2 for Godunov.
+    Against a fine Strang reference on a propagating action potential, the
+    RMS error falls with K and saturates there."""
+    n, t_end = 401, 3.0
+    w = W.single_fiber(t_end_ms=t_end, n_nodes=n)
+
+    def rms(**sc):
+        p = dict(w.params, **sc)
+        dt = p["dt_split"]
+        st = oracle.init_state(p, n, None)
+        s = oracle.run(p, [n], [0], [n // 2], [0, 1], np.array([0.0]), st, 0, int(round(t_end / dt)),
+                       sample_every=int(round(0.1 / dt)))
+        return s
+
+    ref = rms(dt_split=1e-4, dt_0d=2.5e-5, dt_1d=5e-5)
+    err = lambda s: float(np.sqrt(np.mean((s - ref) ** 2)))
+    strang = {K: err(rms(dt_split=4e-3, dt_1d=2e-3, dt_0d=2e-3 / K)) for K in (1, 2, 5, 10)}
+    assert strang[1] > strang[2] > strang[5] >= strang[10] * (1 - 1e-6), strang
+    assert strang[1] > 1.1 * strang[10] and strang[5] < 1.005 * strang[10], strang
+    godunov = {K: err(rms(splitting=3, diffusion=1, dt_split=5e-4, dt_1d=5e-4, dt_0d=5e-4 / K)) for K in (1, 2, 8)}
+    assert godunov[1] >= godunov[2] >= godunov[8] * (1 - 1e-6) and godunov[2] < 1.002 * godunov[8], godunov
+
+
 @pytest.mark.parametrize("splitting", [0, 1, 2, 3])
 def test_single_node_fiber_is_plain_heun_in_every_splitting(splitting):
     # no diffusion on one node: every ordering reduces to n_sub Heun substeps
