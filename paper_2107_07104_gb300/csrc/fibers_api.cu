@@ -70,10 +70,8 @@ struct fib_ctx {
   int64_t graph_launches = 0;
 
   // reaction-step surrogate (FIB_MODE_SURROGATE)
-  int32_t* d_slot_fiber = nullptr;   // surrogate: per-slot code (fiber << 1 | stimulated), -1 padding
-  int32_t* d_net_list = nullptr;     // surrogate: slots of the current step's network nodes
-  unsigned int* d_net_count = nullptr;  // surrogate: their number
-  uint8_t* d_fiber_stim = nullptr;   // per-fiber stimulus substep mask of the current step
+  float* d_sur_list = nullptr;          // surrogate: network-node lists (2 parities x 6 x slots_total)
+  unsigned int* d_sur_count = nullptr;  // surrogate: their lengths [2]
   uint16_t* d_sur_wts = nullptr;     // bf16 weight images
   float* d_sur_bias = nullptr;
   unsigned long long* d_fallback = nullptr;
@@ -232,9 +230,8 @@ void free_layout(fib_ctx* c) {
   dfree(c->d_warps);
   dfree(c->d_rows);
   dfree(c->d_recs);
-  dfree(c->d_slot_fiber);
-  dfree(c->d_net_list);
-  dfree(c->d_net_count);
+  dfree(c->d_sur_list);
+  dfree(c->d_sur_count);
 }
 
 // Builds the padded layout, CTA packing and solver tables for tuning t.
@@ -341,20 +338,9 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   if (c->p.mode == FIB_MODE_SURROGATE && slot > INT32_MAX)
     return fail(c, FIB_EINVAL, "surrogate mode holds slot indices in 32 bits: %lld slots", (long long)slot);
   if (c->p.mode == FIB_MODE_SURROGATE && slot > 0) {
-    // per-slot code for the surrogate kernel: -1 padding, else
-    // (fiber << 1) | (node within the junction's stimulus range)
-    std::vector<int32_t> sf((size_t)slot, -1);
-    const int hw = c->p.stim_half_width;
-    for (int32_t f = 0; f < c->n_fibers; ++f) {
-      const int lo = std::max(fd[f].junction - hw, 0), hi = std::min(fd[f].junction + hw, fd[f].n - 1);
-      for (int32_t i = 0; i < fd[f].n; ++i)
-        sf[(size_t)fd[f].slot + i] = (f << 1) | ((fd[f].mu >= 0 && i >= lo && i <= hi) ? 1 : 0);
-    }
-    CU(c, cudaMalloc(&c->d_slot_fiber, sizeof(int32_t) * sf.size()));
-    CU(c, cudaMemcpy(c->d_slot_fiber, sf.data(), sizeof(int32_t) * sf.size(), cudaMemcpyHostToDevice));
-    CU(c, cudaMalloc(&c->d_net_list, sizeof(int32_t) * sf.size()));
-    CU(c, cudaMalloc(&c->d_net_count, sizeof(unsigned int)));
-    CU(c, cudaMemset(c->d_net_count, 0, sizeof(unsigned int)));
+    CU(c, cudaMalloc(&c->d_sur_list, sizeof(float) * 12 * (size_t)slot));
+    CU(c, cudaMalloc(&c->d_sur_count, 2 * sizeof(unsigned int)));
+    CU(c, cudaMemset(c->d_sur_count, 0, 2 * sizeof(unsigned int)));
   }
   if (!wm.empty()) CU(c, cudaMemcpy(c->d_warps, wm.data(), sizeof(WarpMap) * wm.size(), cudaMemcpyHostToDevice));
   if (fp64) {
@@ -551,59 +537,66 @@ fib_status scatter_state(fib_ctx* c, const float* src) {
 
 }  // namespace
 
-// Surrogate mode: diffusion halves by the step kernel (reaction phase off),
-// the reaction step by the tensor-core surrogate with per-node HH fallback.
+// Surrogate mode, per split step: one launch of the step kernel (the
+// previous step's second diffusion half, this step's first, and the plain
+// reaction of every node, listing the nodes the network handles), then the
+// network pass over that list; after the last step, the second diffusion
+// half alone.  Two diffusion halves in a row are 2 n_cn steps of one
+// operator, so merging them keeps the bits.
 fib_status surrogate_steps(fib_ctx* c, cudaStream_t stream, int64_t n) {
-  if (c->n_ctas == 0) return FIB_OK;
+  if (c->n_ctas == 0 || n <= 0) return FIB_OK;
   StepArgs a = make_args(c);
   a.n_steps = 1;
-  a.step_offset = 0;
-  const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
+  a.sur_list = c->d_sur_list;
+  a.sur_count = c->d_sur_count;
+  a.sur_cap = c->slots_total;
+  for (int k = 0; k < kIn; ++k) {
+    a.sur_env_lo[k] = c->env_lo[k];
+    a.sur_env_hi[k] = c->env_hi[k];
+    a.sur_quiet_lo[k] = c->quiet_lo[k];
+    a.sur_quiet_hi[k] = c->quiet_hi[k];
+  }
+  a.inv_n_sub = 1.0f / (float)c->n_sub;
   SurArgs s{};
   s.u = st_u(c);
   s.m = st_m(c);
   s.h = st_h(c);
   s.n = st_n(c);
-  s.slot_code = c->d_slot_fiber;
-  s.fiber_stim = c->d_fiber_stim;
+  s.list = c->d_sur_list;
+  s.list_count = c->d_sur_count;
+  s.list_cap = c->slots_total;
+  s.step_base = c->d_step;
+  s.real_nodes = c->total;
   s.wts = c->d_sur_wts;
   s.bias = c->d_sur_bias;
   s.fallback_count = c->d_fallback;
-  s.net_list = c->d_net_list;
-  s.net_count = c->d_net_count;
-  s.n_slots = c->slots_total;
-  s.hh = a.hh;
   for (int k = 0; k < kIn; ++k) {
     s.in_mu[k] = c->in_mu[k];
     s.in_inv_sigma[k] = c->in_inv_sigma[k];
-    s.env_lo[k] = c->env_lo[k];
-    s.env_hi[k] = c->env_hi[k];
-    s.quiet_lo[k] = c->quiet_lo[k];
-    s.quiet_hi[k] = c->quiet_hi[k];
   }
   for (int k = 0; k < kOut; ++k) {
     s.out_mu[k] = c->out_mu[k];
     s.out_sigma[k] = c->out_sigma[k];
   }
-  s.n_sub = (int32_t)c->n_sub;
-  s.inv_n_sub = 1.0f / (float)c->n_sub;
-  s.hw = c->p.stim_half_width;
-  a.phases = 1;
-  fib_status st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, stream), "diffusion");
+  const int32_t n_cn = (int32_t)c->n_cn;
+  fib_status st = FIB_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    a.step_offset = i;
+    a.phases = 1 | 2;
+    a.n_cn = i == 0 ? n_cn : 2 * n_cn;
+    st = check_launch(c, launch_split_step_sur(c->K, a, c->n_ctas, stream), "surrogate step");
+    if (st != FIB_OK) return st;
+    s.step_offset = i;
+    st = check_launch(c, launch_sur_net(s, stream), "surrogate network");
+    if (st != FIB_OK) return st;
+    c->launches += 2;
+  }
+  a.phases = 1;  // the last step's second diffusion half (u only)
+  a.n_cn = n_cn;
+  a.step_offset = n;
+  st = check_launch(c, launch_split_step(c->K, false, a, c->n_ctas, stream), "diffusion");
   if (st != FIB_OK) return st;
   ++c->launches;
-  for (int64_t i = 0; i < n; ++i) {
-    st = check_launch(c, launch_fiber_stim(c->d_fibers, c->n_fibers, c->d_mu_off, c->d_fire_k, c->n_mu, c->d_step, i,
-                                           (int)c->n_sub, (int)c->pulse, c->d_fiber_stim, c->d_net_count, stream),
-                      "stimulus");
-    if (st != FIB_OK) return st;
-    st = check_launch(c, launch_sur_step(s, stream), "surrogate");
-    if (st != FIB_OK) return st;
-    a.phases = (i + 1 < n) ? (4 | 1) : 4;
-    st = check_launch(c, launch_split_step(c->K, fp64, a, c->n_ctas, stream), "diffusion");
-    if (st != FIB_OK) return st;
-    c->launches += 3;
-  }
   return FIB_OK;
 }
 
@@ -1079,7 +1072,6 @@ fib_status fibers_load_surrogate(fib_ctx* c, const float* blob, size_t n_floats)
     CU(c, cudaMalloc(&c->d_fallback, sizeof(unsigned long long)));
     CU(c, cudaMemset(c->d_fallback, 0, sizeof(unsigned long long)));
   }
-  if (!c->d_fiber_stim) CU(c, cudaMalloc(&c->d_fiber_stim, std::max<size_t>(c->n_fibers, 1)));
   CU(c, cudaMemcpy(c->d_sur_wts, w.data(), sizeof(uint16_t) * n_w, cudaMemcpyHostToDevice));
   CU(c, cudaMemcpy(c->d_sur_bias, bias.data(), sizeof(float) * bias.size(), cudaMemcpyHostToDevice));
   CU(c, (cudaError_t)sur_set_smem_attributes());
@@ -1155,7 +1147,6 @@ void fibers_destroy(fib_ctx* c) {
   dfree(c->d_quiet);
   dfree(c->d_skipped);
   dfree(c->d_stage);
-  dfree(c->d_fiber_stim);
   dfree(c->d_sur_wts);
   dfree(c->d_sur_bias);
   dfree(c->d_fallback);

@@ -91,6 +91,15 @@ struct StepArgs {
   unsigned long long* skipped;  // fiber-steps skipped
   int32_t adaptive;
   float eq_tol;            // relative change that still counts as equilibrium
+  // surrogate mode (SUR instantiations, one split step per launch): nodes
+  // outside the envelope or inside the quiet box take the plain step here;
+  // the others are listed with their state before the reaction, for the
+  // network pass, which overwrites them
+  float* sur_list;         // per parity 6 arrays of sur_cap: slot (int bits), u, m, h, n, stimulus fraction
+  unsigned int* sur_count; // [2] entries listed, by step parity
+  int64_t sur_cap;
+  float sur_env_lo[5], sur_env_hi[5], sur_quiet_lo[5], sur_quiet_hi[5];
+  float inv_n_sub;
   float vrest;             // resting potential (the test uses V = u + Vrest)
 };
 
@@ -117,6 +126,9 @@ int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, voi
 // (split_step_adaptive.cu).
 int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream);
 int launch_split_step_adaptive(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
+// Surrogate mode's split step (one per launch) with the network-node list
+// (surrogate.cu).
+int launch_split_step_sur(int K, const StepArgs& a, int n_ctas, void* stream);
 int launch_advance(int64_t* step_base, int64_t n, void* stream);
 // dst[coff + i] = src[slot + i] + add for the n real nodes of every fiber.
 int launch_gather(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,

@@ -315,6 +315,73 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
 }
 
 // ---------------------------------------------------------------------------
+// Surrogate mode: the list of nodes for the network pass
+// ---------------------------------------------------------------------------
+
+// Does a node take the plain HH step?  Outside the network's training
+// envelope, or inside the quiet box around rest (where the exact step keeps
+// rest an exact fixed point).
+__device__ __forceinline__ bool sur_plain(const StepArgs& a, const float (&raw)[5]) {
+  bool outside = false, quiet = true;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    outside = outside || !(raw[k] >= a.sur_env_lo[k] && raw[k] <= a.sur_env_hi[k]);
+    quiet = quiet && raw[k] >= a.sur_quiet_lo[k] && raw[k] <= a.sur_quiet_hi[k];
+  }
+  return outside || quiet;
+}
+
+// Lists this thread's network nodes (state before the reaction, stimulus
+// fraction of the split step) with one atomic per warp.
+template <int K>
+__device__ __forceinline__ void list_network_nodes(const StepArgs& a, const float (&u)[K], const float (&m)[K],
+                                                   const float (&h)[K], const float (&n)[K], uint32_t mask,
+                                                   int64_t cur, int64_t fend, int64_t stp, int nreal,
+                                                   int64_t base) {
+  float sfrac = 0.0f;
+  if (mask) {  // substeps of this split step with the pulse on (a private copy of the cursor)
+    int on = 0;
+    for (int k = 0; k < a.n_sub; ++k) {
+      const int64_t kk = stp * a.n_sub + k;
+      while (cur < fend && a.fire_k[cur] + a.pulse <= kk) ++cur;
+      on += (cur < fend) && (a.fire_k[cur] <= kk);
+    }
+    sfrac = (float)on * a.inv_n_sub;
+  }
+  uint32_t netm = 0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float raw[5] = {u[j], m[j], h[j], n[j], ((mask >> j) & 1u) ? sfrac : 0.0f};
+    if (j < nreal && !sur_plain(a, raw)) netm |= 1u << j;
+  }
+  const int cnt = __popc(netm);
+  if (!__any_sync(0xffffffffu, cnt > 0)) return;
+  const int lane = threadIdx.x & 31;
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  unsigned int first = 0;
+  if (lane == 31) first = atomicAdd(a.sur_count + (stp & 1), (unsigned int)incl);
+  first = __shfl_sync(0xffffffffu, first, 31);
+  unsigned int pos = first + (unsigned int)(incl - cnt);
+  float* L = a.sur_list + (stp & 1) * 6 * a.sur_cap;
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    if ((netm >> j) & 1u) {
+      L[pos] = __int_as_float((int)(base + j));
+      L[a.sur_cap + pos] = u[j];
+      L[2 * a.sur_cap + pos] = m[j];
+      L[3 * a.sur_cap + pos] = h[j];
+      L[4 * a.sur_cap + pos] = n[j];
+      L[5 * a.sur_cap + pos] = ((mask >> j) & 1u) ? sfrac : 0.0f;
+      ++pos;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The split-step kernel
 // ---------------------------------------------------------------------------
 
@@ -323,7 +390,11 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
 // ADAPT: adaptive computation (sec:adaptive_computation_for_fiber_based):
 // a fiber in equilibrium with no pulse due skips a whole launch.  Only the
 // adaptive instantiations carry its code.
-template <int K, typename R, bool PACKED, int MINB, bool EXPAPX, bool ADAPT>
+// SUR: surrogate mode's split step (one per launch).  Before the reaction,
+// nodes that the network handles are listed with their state; the plain
+// reaction then runs on every node, and the network pass overwrites the
+// listed ones.
+template <int K, typename R, bool PACKED, int MINB, bool EXPAPX, bool ADAPT, bool SUR>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
     split_step_kernel(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -465,6 +536,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
     // segment 1: substeps [k_split, n_sub)
     for (int seg = 0; seg < 2; ++seg) {
       const int kb = seg ? a.k_split : 0, ke = seg ? a.n_sub : a.k_split;
+      if (SUR && seg == 1 && reaction) list_network_nodes<K>(a, u, m, h, n, mask, cur, fend, stp, nreal, base);
       for (int k = kb; reaction && k < ke; ++k) {
         bool on = false;
         if (mask) {
@@ -527,37 +599,37 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
   }
 }
 
-template <int K, typename R, bool PACKED, int MINB, bool EXPAPX, bool ADAPT>
+template <int K, typename R, bool PACKED, int MINB, bool EXPAPX, bool ADAPT, bool SUR>
 int launch_one(const StepArgs& a, int n_ctas, void* stream) {
   const size_t smem = split_step_smem_bytes(K, sizeof(R) == 8, a.W, ADAPT);
   if (smem > 48 * 1024) {  // opt in to more than the default dynamic shared memory
-    const cudaError_t e = cudaFuncSetAttribute(split_step_kernel<K, R, PACKED, MINB, EXPAPX, ADAPT>,
+    const cudaError_t e = cudaFuncSetAttribute(split_step_kernel<K, R, PACKED, MINB, EXPAPX, ADAPT, SUR>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  split_step_kernel<K, R, PACKED, MINB, EXPAPX, ADAPT>
+  split_step_kernel<K, R, PACKED, MINB, EXPAPX, ADAPT, SUR>
       <<<n_ctas, 32 * a.W, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <int K, typename R, bool EXPAPX, bool ADAPT>
+template <int K, typename R, bool EXPAPX, bool ADAPT, bool SUR>
 int launch_k(const StepArgs& a, int n_ctas, void* stream) {
-  if (sizeof(R) == 8) return launch_one<K, R, false, 2, EXPAPX, ADAPT>(a, n_ctas, stream);  // FP64 solve: one form
+  if (sizeof(R) == 8) return launch_one<K, R, false, 2, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);  // FP64 solve
   if (a.lean)
-    return a.packed ? launch_one<K, R, true, 3, EXPAPX, ADAPT>(a, n_ctas, stream)
-                    : launch_one<K, R, false, 3, EXPAPX, ADAPT>(a, n_ctas, stream);
-  return a.packed ? launch_one<K, R, true, 2, EXPAPX, ADAPT>(a, n_ctas, stream)
-                  : launch_one<K, R, false, 2, EXPAPX, ADAPT>(a, n_ctas, stream);
+    return a.packed ? launch_one<K, R, true, 3, EXPAPX, ADAPT, SUR>(a, n_ctas, stream)
+                    : launch_one<K, R, false, 3, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
+  return a.packed ? launch_one<K, R, true, 2, EXPAPX, ADAPT, SUR>(a, n_ctas, stream)
+                  : launch_one<K, R, false, 2, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
 }
 
-// Dispatch on K for one (R, EXPAPX, ADAPT) family of instantiations.
-template <typename R, bool EXPAPX, bool ADAPT>
+// Dispatch on K for one (R, EXPAPX, ADAPT, SUR) family of instantiations.
+template <typename R, bool EXPAPX, bool ADAPT, bool SUR = false>
 int launch_family(int K, const StepArgs& a, int n_ctas, void* stream) {
   switch (K) {
-    case 4: return launch_k<4, R, EXPAPX, ADAPT>(a, n_ctas, stream);
-    case 8: return launch_k<8, R, EXPAPX, ADAPT>(a, n_ctas, stream);
-    case 12: return launch_k<12, R, EXPAPX, ADAPT>(a, n_ctas, stream);
-    case 16: return launch_k<16, R, EXPAPX, ADAPT>(a, n_ctas, stream);
+    case 4: return launch_k<4, R, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
+    case 8: return launch_k<8, R, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
+    case 12: return launch_k<12, R, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
+    case 16: return launch_k<16, R, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }

@@ -7,10 +7,11 @@
 //   * training kernels (FP32 master weights, optional bfloat16 rounding of
 //     weights and activations in the forward pass, straight-through
 //     gradients) and an Adam update;
-//   * the surrogate step: sur_fallback_kernel applies the plain HH step to
-//     nodes outside the training data's range or near rest and lists the
-//     others; sur_net_kernel evaluates the listed nodes on BF16 tensor cores
-//     (mma.sync m16n8k16, FP32 accumulation) in full tiles of 16.
+//   * the surrogate step: the split-step kernel (SUR instantiations, in this
+//     file) integrates every node with the plain HH step and lists the nodes
+//     inside the training data's range and away from rest; sur_net_kernel
+//     evaluates the listed nodes on BF16 tensor cores (mma.sync m16n8k16,
+//     FP32 accumulation) in full tiles of 16 and writes them over.
 // Network: x (5) -> 128 -> SiLU -> 128 -> SiLU -> 4, predicting the change of
 // (u, m, h, n) over one split step in normalised units.
 #include <cuda_bf16.h>
@@ -269,31 +270,11 @@ __device__ __forceinline__ void to_a_frag(const float (&c0)[4], const float (&c1
   a[3] = pack_bf16(silu(c1[2] + b10), silu(c1[3] + b11));
 }
 
-// Does a node take the plain HH step?  The network only handles nodes inside
-// its training envelope and away from rest: near rest the exact step is cheap
-// and keeps rest an exact fixed point, which a network's small output errors
-// would not.
-__device__ __forceinline__ bool use_plain_step(const SurArgs& a, const float (&raw)[kIn]) {
-  bool outside = false, quiet = true;
-#pragma unroll
-  for (int k = 0; k < kIn; ++k) {
-    outside = outside || !(raw[k] >= a.env_lo[k] && raw[k] <= a.env_hi[k]);
-    quiet = quiet && raw[k] >= a.quiet_lo[k] && raw[k] <= a.quiet_hi[k];
-  }
-  return outside || quiet;
-}
-
 // Per-warp staging of one tile of network nodes: normalised features, the
 // state before the step, and the slot.
 constexpr int kTileRows = 16;
 constexpr int kStageFloats = kTileRows * (kIn + 4 + 1);
 constexpr int kSurThreads = 128;
-// The plain-step pass takes two adjacent slots per lane (one fiber: fiber
-// slots are 4-aligned), 64 per warp; few registers, so many warps hide the
-// latency of the step's state loads.
-constexpr int kFbNodes = 2;
-constexpr int kFbChunk = 32 * kFbNodes;
-constexpr int kFbThreads = 256;
 
 // Inference tile: rows g and g + 8 of 16 staged nodes starting at `base`.
 __device__ __forceinline__ void network_tile(const SurArgs& a, const uint16_t* sW1, const uint16_t* sW2,
@@ -365,101 +346,12 @@ __device__ __forceinline__ void network_tile(const SurArgs& a, const uint16_t* s
   }
 }
 
-// Reaction pass of the surrogate step over every slot.  Nodes outside the
-// network's envelope or near rest take the plain HH step here (the packed
-// Heun code of the split-step kernel, so the same bits as the plain path);
-// the slots of the other nodes are appended to a list for sur_net_kernel,
-// which reads their untouched state.  Node results do not depend on the
-// list's order.
-__global__ void __launch_bounds__(kFbThreads, 4) sur_fallback_kernel(const SurArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t n_chunks = (a.n_slots + kFbChunk - 1) / kFbChunk;
-  unsigned long long fallbacks = 0;
-  for (int64_t chunk = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); chunk < n_chunks;
-       chunk += warps_total) {
-    const int64_t q = chunk * kFbChunk + kFbNodes * lane;  // n_slots is a multiple of 4
-    float u[kFbNodes] = {0, 0}, m[kFbNodes] = {0, 0}, h[kFbNodes] = {0, 0}, n[kFbNodes] = {0, 0};
-    int code[kFbNodes] = {-1, -1};
-    if (q < a.n_slots) {
-      const float2 vu = *reinterpret_cast<const float2*>(a.u + q);
-      const float2 vm = *reinterpret_cast<const float2*>(a.m + q);
-      const float2 vh = *reinterpret_cast<const float2*>(a.h + q);
-      const float2 vn = *reinterpret_cast<const float2*>(a.n + q);
-      const int2 vc = *reinterpret_cast<const int2*>(a.slot_code + q);
-      u[0] = vu.x; u[1] = vu.y; m[0] = vm.x; m[1] = vm.y;
-      h[0] = vh.x; h[1] = vh.y; n[0] = vn.x; n[1] = vn.y;
-      code[0] = vc.x; code[1] = vc.y;
-    }
-    // the two slots share one fiber: its stimulus mask for the step, and
-    // which of them lie in the junction's stimulus range
-    uint32_t jmask = 0, fmask = 0;
-    int fiber = -1;
-#pragma unroll
-    for (int j = 0; j < kFbNodes; ++j)
-      if (code[j] >= 0) {
-        fiber = code[j] >> 1;
-        jmask |= (uint32_t)(code[j] & 1) << j;
-      }
-    if (jmask) fmask = a.fiber_stim[fiber];
-    const float sfrac = (float)__popc(fmask) * a.inv_n_sub;
-    uint32_t fbm = 0, netm = 0;
-#pragma unroll
-    for (int j = 0; j < kFbNodes; ++j) {
-      if (code[j] < 0) continue;
-      const float raw[kIn] = {u[j], m[j], h[j], n[j], ((jmask >> j) & 1u) ? sfrac : 0.0f};
-      if (use_plain_step(a, raw)) fbm |= 1u << j;
-      else netm |= 1u << j;
-    }
-    if (fbm) {
-      float uu[kFbNodes] = {u[0], u[1]}, mm[kFbNodes] = {m[0], m[1]};
-      float hh[kFbNodes] = {h[0], h[1]}, nn[kFbNodes] = {n[0], n[1]};
-      for (int k = 0; k < a.n_sub; ++k) {
-        if (jmask && ((fmask >> k) & 1u)) heun_nodes_packed<kFbNodes, true, false>(uu, mm, hh, nn, a.hh, jmask);
-        else heun_nodes_packed<kFbNodes, false, false>(uu, mm, hh, nn, a.hh, 0u);
-      }
-      if (fbm == 0x3u) {
-        *reinterpret_cast<float2*>(a.u + q) = make_float2(uu[0], uu[1]);
-        *reinterpret_cast<float2*>(a.m + q) = make_float2(mm[0], mm[1]);
-        *reinterpret_cast<float2*>(a.h + q) = make_float2(hh[0], hh[1]);
-        *reinterpret_cast<float2*>(a.n + q) = make_float2(nn[0], nn[1]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < kFbNodes; ++j)
-          if ((fbm >> j) & 1u) {
-            a.u[q + j] = uu[j];
-            a.m[q + j] = mm[j];
-            a.h[q + j] = hh[j];
-            a.n[q + j] = nn[j];
-          }
-      }
-      fallbacks += __popc(fbm);
-    }
-    // append the network nodes: one atomic per warp
-    const int cnt = __popc(netm);
-    if (__any_sync(0xffffffffu, cnt > 0)) {
-      int incl = cnt;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
-      }
-      unsigned int base = 0;
-      if (lane == 31) base = atomicAdd(a.net_count, (unsigned int)incl);
-      base = __shfl_sync(0xffffffffu, base, 31);
-      unsigned int pos = base + (unsigned int)(incl - cnt);
-#pragma unroll
-      for (int j = 0; j < kFbNodes; ++j)
-        if ((netm >> j) & 1u) a.net_list[pos++] = (int32_t)(q + j);
-    }
-  }
-  // one atomic per warp: same-address atomics from every thread serialise
-  const unsigned int wsum = __reduce_add_sync(0xffffffffu, (unsigned int)fallbacks);
-  if (lane == 0 && wsum) atomicAdd(a.fallback_count, (unsigned long long)wsum);
-}
-
-// Network pass: the listed nodes in tiles of 16 on the tensor cores.  Each
-// warp stages one tile's inputs in shared memory, then evaluates it.
+// Network pass of a surrogate split step: the nodes the step kernel listed
+// (with their state before the reaction) in tiles of 16 on the tensor
+// cores, written over the plain step's result.  Each warp stages one tile's
+// inputs in shared memory, then evaluates it.  Node results do not depend
+// on the list's order.  Block 0 also empties the other parity's list for
+// the next step and counts the step's plain-path node updates.
 __global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint16_t* sW1 = reinterpret_cast<uint16_t*>(smem_raw);  // [kHid][kW1Stride]
@@ -467,7 +359,13 @@ __global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
   uint16_t* sW3 = sW2 + kHid * kW2Stride;                  // [8][kW2Stride]
   float* sB = reinterpret_cast<float*>(sW3 + 8 * kW2Stride);  // b1[128], b2[128], b3[8]
   float* stage = sB + 2 * kHid + 8;
-  const int64_t count = *a.net_count;
+  const int64_t stp = *a.step_base + a.step_offset;
+  const int par = (int)(stp & 1);
+  const int64_t count = a.list_count[par];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.list_count[par ^ 1] = 0;
+    atomicAdd(a.fallback_count, (unsigned long long)(a.real_nodes - count));
+  }
   if (count == 0) return;
   {
     const uint32_t* gw = reinterpret_cast<const uint32_t*>(a.wts);
@@ -481,6 +379,7 @@ __global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
   float* sx = stage + (threadIdx.x >> 5) * kStageFloats;  // [kTileRows][kIn]
   float* sy = sx + kTileRows * kIn;                       // [kTileRows][4]
   int* sq = reinterpret_cast<int*>(sy + kTileRows * 4);   // [kTileRows]
+  const float* L = a.list + par * 6 * a.list_cap;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t n_tiles = (count + kTileRows - 1) / kTileRows;
   for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < n_tiles;
@@ -488,46 +387,19 @@ __global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
     const int64_t e0 = tile * kTileRows;
     const int rows = (int)(count - e0 < kTileRows ? count - e0 : kTileRows);
     if (lane < rows) {
-      const int64_t q = a.net_list[e0 + lane];
-      const int code = a.slot_code[q];
-      const uint32_t fmask = (code & 1) ? a.fiber_stim[code >> 1] : 0u;
-      const float raw[kIn] = {a.u[q], a.m[q], a.h[q], a.n[q], (float)__popc(fmask) * a.inv_n_sub};
+      const int64_t e = e0 + lane;
+      float raw[kIn];
+#pragma unroll
+      for (int k = 0; k < kIn; ++k) raw[k] = L[(1 + k) * a.list_cap + e];
 #pragma unroll
       for (int k = 0; k < kIn; ++k) sx[lane * kIn + k] = (raw[k] - a.in_mu[k]) * a.in_inv_sigma[k];
 #pragma unroll
       for (int k = 0; k < 4; ++k) sy[lane * 4 + k] = raw[k];
-      sq[lane] = (int)q;
+      sq[lane] = __float_as_int(L[e]);
     }
     __syncwarp();
     network_tile(a, sW1, sW2, sW3, sB, sx, sy, sq, 0, rows, g, t);
     __syncwarp();  // the staging area is rewritten by the next tile
-  }
-}
-
-// Stimulus substep mask of every fiber for one split step.
-__global__ void fiber_stim_kernel(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off,
-                                  const int64_t* fire_k, int32_t n_mu, const int64_t* step_base, int64_t step_offset,
-                                  int n_sub, int pulse, uint8_t* out, unsigned int* net_count) {
-  if (net_count && blockIdx.x == 0 && threadIdx.x == 0) *net_count = 0;  // the step's network list starts empty
-  for (int32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < n_fibers; f += gridDim.x * blockDim.x) {
-    const int mu = fibers[f].mu;
-    uint8_t mask = 0;
-    if (mu >= 0 && mu < n_mu) {
-      const int64_t k0 = (*step_base + step_offset) * n_sub;
-      int64_t lo = mu_off[mu], hi = mu_off[mu + 1];
-      const int64_t end = hi;
-      while (lo < hi) {  // first firing whose pulse has not ended at k0
-        const int64_t mid = (lo + hi) >> 1;
-        if (fire_k[mid] + pulse <= k0) lo = mid + 1;
-        else hi = mid;
-      }
-      for (int k = 0; k < n_sub; ++k) {
-        int64_t cur = lo;
-        while (cur < end && fire_k[cur] + pulse <= k0 + k) ++cur;
-        if (cur < end && fire_k[cur] <= k0 + k) mask |= (uint8_t)(1u << k);
-      }
-    }
-    out[f] = mask;
   }
 }
 
@@ -594,27 +466,14 @@ int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream)
   return (int)cudaGetLastError();
 }
 
-int launch_sur_step(const SurArgs& a, void* stream) {
-  const int64_t chunks = (a.n_slots + kFbChunk - 1) / kFbChunk;
-  const int64_t warps = kFbThreads / 32;
-  int64_t blocks = (chunks + warps - 1) / warps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (blocks < 1) blocks = 1;
-  sur_fallback_kernel<<<(int)blocks, kFbThreads, 0, (cudaStream_t)stream>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return (int)e;
-  // the list's length is known on the device only: a fixed grid strides over it
+int launch_sur_net(const SurArgs& a, void* stream) {
+  // the list's length exists on the device only: a fixed grid strides over it
   sur_net_kernel<<<152 * 4, kSurThreads, sur_smem_bytes(), (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
-int launch_fiber_stim(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off, const int64_t* fire_k,
-                      int32_t n_mu, const int64_t* step_base, int64_t step_offset, int n_sub, int pulse, uint8_t* out,
-                      unsigned int* net_count, void* stream) {
-  const int blocks = n_fibers > 0 ? (n_fibers + 255) / 256 : 1;
-  fiber_stim_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(fibers, n_fibers, mu_off, fire_k, n_mu, step_base,
-                                                             step_offset, n_sub, pulse, out, net_count);
-  return (int)cudaGetLastError();
+int launch_split_step_sur(int K, const StepArgs& a, int n_ctas, void* stream) {
+  return launch_family<float, false, false, true>(K, a, n_ctas, stream);
 }
 
 int sur_set_smem_attributes() {

@@ -25,21 +25,17 @@ constexpr int kW2Stride = 136;
 
 struct SurArgs {
   float *u, *m, *h, *n;         // padded state arrays (u = V - Vrest)
-  const int32_t* slot_code;     // per slot: -1 padding, else (fiber << 1) | (node in its junction's stimulus range)
-  const uint8_t* fiber_stim;    // stimulus substep mask of each fiber for this step
+  const float* list;            // per parity 6 arrays of list_cap: slot (int bits), u, m, h, n, stimulus fraction
+  unsigned int* list_count;     // [2] entries of each parity's list
+  int64_t list_cap;
+  const int64_t* step_base;     // device step counter; this step is *step_base + step_offset
+  int64_t step_offset;
+  int64_t real_nodes;           // nodes of the context (plain-path count)
   const uint16_t* wts;          // bf16 images W1 | W2 | W3
   const float* bias;            // b1 (128) | b2 (128) | b3 (8)
   unsigned long long* fallback_count;
-  int32_t* net_list;            // slots of the step's network nodes (capacity n_slots)
-  unsigned int* net_count;      // their number (reset by the step's stimulus kernel)
-  int64_t n_slots;
-  HHConst hh;
   float in_mu[kIn], in_inv_sigma[kIn];
   float out_mu[kOut], out_sigma[kOut];
-  float env_lo[kIn], env_hi[kIn];      // training envelope: outside -> plain HH
-  float quiet_lo[kIn], quiet_hi[kIn];  // neighbourhood of rest: inside -> plain HH
-  int32_t n_sub, hw;
-  float inv_n_sub;              // 1 / n_sub (stimulus fraction of a split step)
 };
 
 size_t sur_smem_bytes();
@@ -52,9 +48,6 @@ int launch_mlp_forward(const float* th, int quantize, const float* x, int64_t B,
 int launch_adam(float* th, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2, float eps,
                 int64_t t, void* stream);
 int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream);
-int launch_sur_step(const SurArgs& a, void* stream);
-int launch_fiber_stim(const FiberDesc* fibers, int32_t n_fibers, const int64_t* mu_off, const int64_t* fire_k,
-                      int32_t n_mu, const int64_t* step_base, int64_t step_offset, int n_sub, int pulse, uint8_t* out,
-                      unsigned int* net_count, void* stream);
+int launch_sur_net(const SurArgs& a, void* stream);
 
 }  // namespace fib
