@@ -228,7 +228,7 @@ def accuracy_vs_oracle(tune, steps):
     d = v - v_ref
     return {"fibers": int(sub.n_fibers), "split_steps": int(steps), "max_abs_mv": float(np.max(np.abs(d))),
             "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(v_ref)), "tolerance_mv": 0.5,
-            "depolarised_nodes": int(np.sum(v_ref > v_ref.min() + 10.0))}
+            "nodes_above_rest_plus_15_mv": int(np.sum(v_ref > sub.params["Vrest"] + 15.0))}
 
 
 def run_reference(args, world, rank):
