@@ -360,6 +360,7 @@ def run_gpu(args, world, rank, local, dist):
     adaptive = None if args.no_adaptive else adaptive_leg(args, w, tune, stream, dev, total, per_gpu_rate)
     schemes = None if args.no_schemes else schemes_leg(args, w, tune, stream, dev, total)
     expapx = None if args.no_exp_approx else exp_approx_leg(args, w, tune, stream, dev, total, per_gpu_rate)
+    full = None if args.no_full_scale else full_scale_leg(stream, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
@@ -392,6 +393,7 @@ def run_gpu(args, world, rank, local, dist):
         "adaptive": adaptive,
         "schemes": schemes,
         "exp_approx": expapx,
+        "full_scale": full,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -590,6 +592,40 @@ def schemes_leg(args, w, tune, stream, dev, total, sim_ms=3.0):
     return out
 
 
+def full_scale_leg(stream, dev, plain_steps=500, sur_steps=200):
+    """The full-scale bundle (67600 fibers x 1481 nodes = 1.0e8 nodes, 200
+    MUs): plain FP32 and surrogate node-updates/s and HBM fractions on one
+    GPU, each timed after a warm-up with the state resident."""
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+    from paper_2107_07104_gb300 import surrogate as S
+    w = W.bundle_67600(seed=5, t_end_ms=100.0)
+    hbm_peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    out = {"workload": "bundle 67600 fibers x 1481 nodes (260x260), 200 MUs, Poisson 10-30 Hz",
+           "nodes": int(w.total_nodes)}
+    for name, mode, steps in (("plain_fp32", F.FIB_MODE_FP32, plain_steps),
+                              ("surrogate", F.FIB_MODE_SURROGATE, sur_steps)):
+        with F.Fibers.from_workload(w, stream=stream, mode=mode) as fib:
+            if mode == F.FIB_MODE_SURROGATE:
+                F.fibers_load_surrogate(fib.ctx, S.load_blob())
+            fib.step(max(steps // 10, 3))
+            fib.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            fib.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            finite = bool(np.all(np.isfinite(fib.read_vm())))
+        rate = float(w.total_nodes) * steps / (ms / 1e3)
+        out[name] = {"node_updates_per_s": rate, "ms_per_step": ms / steps, "steps": steps, "finite": finite,
+                     "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak}
+    out["surrogate_vs_plain"] = out["surrogate"]["node_updates_per_s"] / out["plain_fp32"]["node_updates_per_s"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -610,6 +646,7 @@ def main():
     ap.add_argument("--no-adaptive", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-exp-approx", action="store_true")
+    ap.add_argument("--no-full-scale", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
