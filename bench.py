@@ -613,15 +613,17 @@ def full_scale_leg(stream, dev, plain_steps=500, sur_steps=200):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
-            e0.record(stream)
-            fib.step(steps)
-            e1.record(stream)
-            e1.synchronize()
+            with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+                e0.record(stream)
+                fib.step(steps)
+                e1.record(stream)
+                e1.synchronize()
             ms = e0.elapsed_time(e1)
             finite = bool(np.all(np.isfinite(fib.read_vm())))
         rate = float(w.total_nodes) * steps / (ms / 1e3)
         out[name] = {"node_updates_per_s": rate, "ms_per_step": ms / steps, "steps": steps, "finite": finite,
-                     "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak}
+                     "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak,
+                     "clocks": clk.summary()}
     out["surrogate_vs_plain"] = out["surrogate"]["node_updates_per_s"] / out["plain_fp32"]["node_updates_per_s"]
     return out
 
