@@ -639,7 +639,7 @@ def main():
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--graph-steps", type=int, default=1000)
     ap.add_argument("--reaction-pairs", type=int, default=0, help="1 scalar, 2 packed FP32x2, 0 auto")
-    ap.add_argument("--ctas-per-sm", type=int, default=0, help="register budget: 2 or 3 CTAs per SM, 0 auto")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="register budget: 2, 3 or 4 CTAs per SM, 0 auto")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-fibers", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=1500)

@@ -134,8 +134,9 @@ typedef struct {
   int32_t graph_steps;       /* split steps per captured CUDA graph (0 = no graphs) */
   int32_t reaction_pairs;    /* 1: one node per FP32 instruction; 2: node pairs with packed
                                 FP32x2 instructions (same results bit for bit); 0: automatic */
-  int32_t ctas_per_sm;       /* register budget of the step kernel: 2 (up to 128 registers per
-                                thread) or 3 (up to 85, more warps per SM); 0: automatic */
+  int32_t ctas_per_sm;       /* register budget of the step kernel, as CTAs of 256 threads per
+                                SM: 2 (up to 128 registers per thread), 3 (up to 80) or 4 (up to
+                                64, more warps per SM, a few spills at K = 8); 0: automatic */
 } fib_tuning;
 
 /* Creates a context for n_fibers fibers and copies the inputs to the device.
@@ -298,9 +299,17 @@ fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float*
                               float* out, void* cuda_stream);
 
 /* One Adam update of n parameters in place (Kingma & Ba 2015, with bias
- * correction for step t >= 1).  All buffers on the device.  Asynchronous. */
+ * correction for step t >= 1).  All buffers on the device.
+ *   theta_avg  NULL, or n floats updated after the step to the exponential
+ *              moving average of the weights (Polyak averaging in its
+ *              exponential form): theta_avg = avg_decay * theta_avg +
+ *              (1 - avg_decay) * theta.  The caller initialises it (for
+ *              example with theta before the first step).
+ *   avg_decay  in [0, 1]; ignored when theta_avg is NULL.
+ * Asynchronous.  Errors: FIB_EINVAL (n < 1, t < 1, a NULL buffer, avg_decay
+ * outside [0, 1]), FIB_ECUDA. */
 fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad, int64_t n, float lr, float beta1,
-                            float beta2, float eps, int64_t t, void* cuda_stream);
+                            float beta2, float eps, int64_t t, float* theta_avg, float avg_decay, void* cuda_stream);
 
 /* Per-column mean, standard deviation, minimum and maximum of a device matrix
  * X (n x cols, row-major) into out (host, 4 x cols doubles, column by column:

@@ -128,6 +128,12 @@ def adam_step(theta, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
+def weight_average(avg, theta, decay):
+    """Exponential moving average of the weights after a step (Polyak
+    averaging, Polyak & Juditsky 1992, in its exponential form)."""
+    return decay * avg + (1 - decay) * theta
+
+
 def init_params(seed, scale=1.0):
     """He-style uniform initialisation (for tests and as the training start)."""
     rng = np.random.default_rng(seed)

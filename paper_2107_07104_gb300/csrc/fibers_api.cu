@@ -249,8 +249,8 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   if (W < w_max) return fail(c, FIB_EINVAL, "warps_per_cta %d < %d warps needed by the longest fiber", W, w_max);
   if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
   if (t.reaction_pairs < 0 || t.reaction_pairs > 2) return fail(c, FIB_EINVAL, "reaction_pairs must be 0, 1 or 2");
-  if (t.ctas_per_sm != 0 && t.ctas_per_sm != 2 && t.ctas_per_sm != 3)
-    return fail(c, FIB_EINVAL, "ctas_per_sm must be 0, 2 or 3");
+  if (t.ctas_per_sm != 0 && (t.ctas_per_sm < 2 || t.ctas_per_sm > 4))
+    return fail(c, FIB_EINVAL, "ctas_per_sm must be 0, 2, 3 or 4");
 
   // length classes
   std::map<int32_t, int> cls;
@@ -262,11 +262,12 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
       tw.push_back(32 * warps_for(n, K));
     }
   SolverTables tab;
-  if (!lens.empty() && !build_solver_tables(K, c->r, lens, tw, &tab))
+  const bool fp64_tables = c->p.mode == FIB_MODE_FP64_THOMAS;
+  if (!lens.empty() && !build_solver_tables(K, c->r, lens, tw, fp64_tables, &tab))
     return fail(c, FIB_EINVAL, "tridiagonal tables: zero pivot (r = %g)", c->r);
   if (lens.empty()) {  // keep valid (unused) tables
     std::vector<int32_t> one{1}, t1{32};
-    build_solver_tables(K, c->r, one, t1, &tab);
+    build_solver_tables(K, c->r, one, t1, fp64_tables, &tab);
   }
 
   // slots and packing: fibers by warp count (descending), next-fit into CTAs
@@ -431,7 +432,7 @@ StepArgs make_args(fib_ctx* c) {
   a.rec_stride = c->rec_stride;
   a.W = c->W;
   a.packed = c->tune.reaction_pairs == 2 ? 1 : 0;
-  a.lean = c->tune.ctas_per_sm == 3 ? 1 : 0;
+  a.occ = c->tune.ctas_per_sm;
   a.phases = 7;
   a.adaptive = (c->p.flags & FIB_FLAG_ADAPTIVE) ? 1 : 0;
   a.quiet = c->d_quiet;
@@ -963,7 +964,7 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
     if (w_max * 2 <= kMaxWarpsPerCta && auto_W(w_max) != w_max) Ws.push_back(w_max);
     for (int W : Ws)
      for (int pairs : {1, 2})
-      for (int occ : {2, 3}) {
+      for (int occ : {2, 3, 4}) {
       fib_tuning t{K, W, start.steps_per_launch, start.graph_steps, pairs, occ};
       if (build_layout(c, t) != FIB_OK) continue;
       if (need > 0 && scatter_state(c, keep) != FIB_OK) continue;
@@ -1114,9 +1115,11 @@ fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float*
 }
 
 fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad, int64_t n, float lr, float beta1,
-                            float beta2, float eps, int64_t t, void* cuda_stream) {
+                            float beta2, float eps, int64_t t, float* theta_avg, float avg_decay, void* cuda_stream) {
   if (n < 1 || t < 1 || !theta || !m || !v || !grad) return fail(nullptr, FIB_EINVAL, "bad size, step or buffer");
-  const int e = launch_adam(theta, m, v, grad, n, lr, beta1, beta2, eps, t, cuda_stream);
+  if (theta_avg && !(avg_decay >= 0.0f && avg_decay <= 1.0f))
+    return fail(nullptr, FIB_EINVAL, "avg_decay must be in [0, 1]");
+  const int e = launch_adam(theta, m, v, grad, n, lr, beta1, beta2, eps, t, theta_avg, avg_decay, cuda_stream);
   if (e) return fail(nullptr, FIB_ECUDA, "adam kernel: %s", cudaGetErrorString((cudaError_t)e));
   return FIB_OK;
 }

@@ -84,7 +84,7 @@ struct StepArgs {
   int32_t rec_stride;      // elements per thread record
   int32_t W;               // warps per CTA
   int32_t packed;          // 1: reaction step on node pairs with FP32x2 arithmetic
-  int32_t lean;            // 1: kernel built for 3 CTAs of 256 threads per SM (<= 85 registers)
+  int32_t occ;             // the kernel's register budget, as CTAs of 256 threads per SM (2, 3 or 4)
   int32_t phases;          // bit 0: first diffusion phase, bit 1: reaction, bit 2: second diffusion phase
   // adaptive computation: skip fibers in equilibrium with no pulse due
   uint8_t* quiet;          // per fiber: 1 = passed the equilibrium test at the end of its last launch
@@ -116,9 +116,10 @@ struct SolverTables {
 
 // Builds the tables for fiber lengths `lengths` (distinct values, one class
 // each), K nodes per thread, threads_per_class[i] threads for class i, and
-// CN coefficient r.  Returns false on a zero pivot.
+// CN coefficient r; fp64_solve selects the PCR cutoff of the FP64 solve.
+// Returns false on a zero pivot.
 bool build_solver_tables(int K, double r, const std::vector<int32_t>& lengths,
-                         const std::vector<int32_t>& threads_per_class, SolverTables* out);
+                         const std::vector<int32_t>& threads_per_class, bool fp64_solve, SolverTables* out);
 
 // Device entry points (split_step.cu).
 int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);

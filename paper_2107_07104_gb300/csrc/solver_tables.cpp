@@ -21,10 +21,15 @@
 //   4. x_s and the interior unknowns follow from steps 1-2.
 // Everything except the right-hand-side terms depends on the matrix only,
 // which is constant in time, so it is computed here once, in FP64.  PCR
-// stops after the level at which every remaining coupling is below 2^-40
-// (relative to the unit diagonal): from there on the equations are decoupled
-// to far below FP32 and FP64 rounding of the solution, so the truncated solve
-// equals the exact one up to rounding.
+// stops after the level at which every remaining coupling (relative to the
+// unit diagonal) is below a cutoff, so each dropped term moves a solution
+// value by less than the cutoff times the largest |u| of the fiber:
+//   - FP32 solve: 2^-32.  Its tables are rounded to FP32 (relative error
+//     up to 2^-24) and its state is stored in FP32, so the dropped terms
+//     are at least 256 times smaller than rounding the solve already does.
+//   - FP64 solve: 2^-40, 2^16 times below the FP32 rounding of the state
+//     it writes back.
+// Either way the truncated solve equals the exact one up to rounding.
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -167,12 +172,10 @@ double max_coupling(const std::vector<double>& A, const std::vector<double>& C) 
   return m;
 }
 
-constexpr double kDecoupled = 9.094947017729282e-13;  // 2^-40
-
-int levels_needed(Reduced red) {
+int levels_needed(Reduced red, double cutoff) {
   int L = 0;
   const int T = (int)red.A.size();
-  for (int s = 1; max_coupling(red.A, red.C) > kDecoupled && s < T && L < kMaxLevels; s *= 2, ++L)
+  for (int s = 1; max_coupling(red.A, red.C) > cutoff && s < T && L < kMaxLevels; s *= 2, ++L)
     if (!pcr_level(red.A, red.C, s, nullptr)) return -1;
   return L;
 }
@@ -180,7 +183,7 @@ int levels_needed(Reduced red) {
 }  // namespace
 
 bool build_solver_tables(int K, double r, const std::vector<int32_t>& lengths,
-                         const std::vector<int32_t>& threads_per_class, SolverTables* out) {
+                         const std::vector<int32_t>& threads_per_class, bool fp64_solve, SolverTables* out) {
   if (K < 4 || lengths.size() != threads_per_class.size()) return false;
   out->K = K;
   const size_t nc = lengths.size();
@@ -190,7 +193,7 @@ bool build_solver_tables(int K, double r, const std::vector<int32_t>& lengths,
     const int32_t N = lengths[i];
     const double rf = N > 1 ? r : 0.0;
     if (!reduced_system(N, rf, K, threads_per_class[i], &red[i])) return false;
-    const int l = levels_needed(red[i]);
+    const int l = levels_needed(red[i], fp64_solve ? 0x1p-40 : 0x1p-32);
     if (l < 0) return false;
     L = l > L ? l : L;
   }

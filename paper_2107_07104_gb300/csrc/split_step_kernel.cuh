@@ -615,7 +615,10 @@ int launch_one(const StepArgs& a, int n_ctas, void* stream) {
 template <int K, typename R, bool EXPAPX, bool ADAPT, bool SUR>
 int launch_k(const StepArgs& a, int n_ctas, void* stream) {
   if (sizeof(R) == 8) return launch_one<K, R, false, 2, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);  // FP64 solve
-  if (a.lean)
+  if (a.occ == 4)
+    return a.packed ? launch_one<K, R, true, 4, EXPAPX, ADAPT, SUR>(a, n_ctas, stream)
+                    : launch_one<K, R, false, 4, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
+  if (a.occ == 3)
     return a.packed ? launch_one<K, R, true, 3, EXPAPX, ADAPT, SUR>(a, n_ctas, stream)
                     : launch_one<K, R, false, 3, EXPAPX, ADAPT, SUR>(a, n_ctas, stream);
   return a.packed ? launch_one<K, R, true, 2, EXPAPX, ADAPT, SUR>(a, n_ctas, stream)

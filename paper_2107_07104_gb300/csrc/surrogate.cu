@@ -194,13 +194,15 @@ __global__ void mse_kernel(const float* out, const float* target, int64_t n, flo
 }
 
 __global__ void adam_kernel(float* th, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
+                            float eps, float c1, float c2, float* avg, float d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float mi = b1 * m[i] + (1.0f - b1) * g[i];
     const float vi = b2 * v[i] + (1.0f - b2) * g[i] * g[i];
     m[i] = mi;
     v[i] = vi;
-    th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float ti = th[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    th[i] = ti;
+    if (avg != nullptr) avg[i] = d * avg[i] + (1.0f - d) * ti;  // exponential weight average
   }
 }
 
@@ -455,9 +457,10 @@ int launch_mlp_forward(const float* th, int quantize, const float* x, int64_t B,
 }
 
 int launch_adam(float* th, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2, float eps,
-                int64_t t, void* stream) {
+                int64_t t, float* avg, float avg_decay, void* stream) {
   const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
-  adam_kernel<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(th, m, v, g, n, lr, b1, b2, eps, c1, c2);
+  adam_kernel<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(th, m, v, g, n, lr, b1, b2, eps, c1, c2,
+                                                                         avg, avg_decay);
   return (int)cudaGetLastError();
 }
 

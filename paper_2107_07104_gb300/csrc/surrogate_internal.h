@@ -46,7 +46,7 @@ int launch_mlp_train_step(const float* th, int quantize, const float* x, const f
                           float* grad, float* loss, void* stream);
 int launch_mlp_forward(const float* th, int quantize, const float* x, int64_t B, float* ws, float* out, void* stream);
 int launch_adam(float* th, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2, float eps,
-                int64_t t, void* stream);
+                int64_t t, float* avg, float avg_decay, void* stream);
 int launch_stats(const float* X, int64_t n, int cols, double* out, void* stream);
 int launch_sur_net(const SurArgs& a, void* stream);
 

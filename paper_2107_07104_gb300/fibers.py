@@ -115,7 +115,7 @@ def load(build_if_missing: bool = True):
         L.fibers_hh_reaction.argtypes = [P(FibParams), i64, vp, vp, vp, vp]
         L.fibers_mlp_train_step.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp, vp]
         L.fibers_mlp_forward.argtypes = [vp, i32, vp, i64, vp, vp, vp]
-        L.fibers_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]
+        L.fibers_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, f32, vp]
         L.fibers_feature_stats.argtypes = [vp, i64, i32, f64p, vp]
         for name in ("fibers_load_surrogate", "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward",
                      "fibers_adam_step", "fibers_feature_stats"):
@@ -307,9 +307,12 @@ def fibers_mlp_forward(theta, quantize: bool, x, workspace, out, stream=None) ->
                                      _dev(out), _stream_ptr(stream)), None)
 
 
-def fibers_adam_step(theta, m, v, grad, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+def fibers_adam_step(theta, m, v, grad, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, theta_avg=None, avg_decay=0.999,
+                     stream=None) -> None:
+    """Adam step; with theta_avg, also the exponential average of the weights."""
+    avg = None if theta_avg is None else _dev(theta_avg)
     _check(load().fibers_adam_step(_dev(theta), _dev(m), _dev(v), _dev(grad), theta.numel(), float(lr), float(beta1),
-                                   float(beta2), float(eps), int(t), _stream_ptr(stream)), None)
+                                   float(beta2), float(eps), int(t), avg, float(avg_decay), _stream_ptr(stream)), None)
 
 
 def fibers_feature_stats(X, stream=None) -> np.ndarray:

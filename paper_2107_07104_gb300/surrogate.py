@@ -115,10 +115,16 @@ def outside_box(X, lo, hi):
 
 
 def train(X, Y, epochs: int = 6, batch: int = 8192, lr: float = 2e-3, lr_end: float = 2e-5, seed: int = 0,
-          quantize: bool = True, log: Optional[List[float]] = None, quiet=None) -> np.ndarray:
+          quantize: bool = True, log: Optional[List[float]] = None, quiet=None,
+          avg_decay: Optional[float] = 0.999) -> np.ndarray:
     """Adam on the normalised data (cosine learning-rate decay); returns the
     blob for fibers_load_surrogate.  Samples inside the quiet box (handled by
-    the plain step at run time) are left out."""
+    the plain step at run time) are left out.
+
+    The blob carries the exponential moving average of the weights over the
+    steps (decay avg_decay; None: the last step's weights).  On held-out
+    bundles the average's activation times varied far less between training
+    seeds than the last weights' did."""
     torch = _torch()
     dev = X.device
     if quiet is None:
@@ -141,6 +147,7 @@ def train(X, Y, epochs: int = 6, batch: int = 8192, lr: float = 2e-3, lr_end: fl
     theta = torch.as_tensor(_he_uniform(seed), device=dev).contiguous()
     m = torch.zeros_like(theta)
     v = torch.zeros_like(theta)
+    avg = None if avg_decay is None else theta.clone()
     grad = torch.zeros_like(theta)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     work = torch.empty(batch * F.SUR_WORK_PER_SAMPLE, dtype=torch.float32, device=dev)
@@ -159,10 +166,11 @@ def train(X, Y, epochs: int = 6, batch: int = 8192, lr: float = 2e-3, lr_end: fl
             F.fibers_mlp_train_step(theta, quantize, xb, yb, work, grad, loss)
             t += 1
             rate = lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * t / total))
-            F.fibers_adam_step(theta, m, v, grad, rate, t)
+            F.fibers_adam_step(theta, m, v, grad, rate, t, theta_avg=avg, avg_decay=avg_decay or 0.0)
             if log is not None and (t % 50 == 0 or t == total):
                 log.append(float(loss.item()))
-    return make_blob(theta.cpu().numpy(), in_mu, in_sigma, out_mu, out_sigma, env_lo, env_hi, quiet[0], quiet[1])
+    final = theta if avg is None else avg
+    return make_blob(final.cpu().numpy(), in_mu, in_sigma, out_mu, out_sigma, env_lo, env_hi, quiet[0], quiet[1])
 
 
 def make_blob(theta, in_mu, in_sigma, out_mu, out_sigma, env_lo, env_hi, quiet_lo, quiet_hi) -> np.ndarray:

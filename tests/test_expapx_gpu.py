@@ -36,7 +36,7 @@ def test_exp_star_reaction_forms_are_bitwise_identical():
     w = edge_workload(400, seed=31)
     w.params["exp_approx"] = 1
     a = gpu_checkpoints(w, [200, 400], tuning=dict(nodes_per_thread=8, reaction_pairs=1, ctas_per_sm=2))
-    for pairs, occ in ((2, 2), (2, 3), (1, 3)):
+    for pairs, occ in ((2, 2), (2, 3), (1, 3), (2, 4)):
         b = gpu_checkpoints(w, [200, 400], tuning=dict(nodes_per_thread=8, reaction_pairs=pairs, ctas_per_sm=occ))
         assert np.array_equal(a, b), (pairs, occ)
 

@@ -67,3 +67,15 @@ def test_adam_first_step_moves_each_parameter_by_lr():
     g = np.array([0.3, -2.0, 1e-3, 0.0])
     th, m, v = mlp.adam_step(np.zeros(4), np.zeros(4), np.zeros(4), g, 1, lr=0.01, eps=1e-12)
     assert np.allclose(th[:3], -0.01 * np.sign(g[:3]), rtol=1e-6) and th[3] == 0.0
+
+
+def test_weight_average_closed_form():
+    # a constant weight c, averaged from a0 over k steps: c + (a0 - c) d^k;
+    # with decay 0 the average is the latest weight, with decay 1 the start
+    a, c, d = np.array([2.0, -1.0]), np.array([0.5, 3.0]), 0.9
+    avg = a.copy()
+    for _ in range(25):
+        avg = mlp.weight_average(avg, c, d)
+    assert np.allclose(avg, c + (a - c) * d ** 25, rtol=1e-12)
+    assert np.array_equal(mlp.weight_average(a, c, 0.0), c)
+    assert np.array_equal(mlp.weight_average(a, c, 1.0), a)

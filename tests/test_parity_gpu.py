@@ -190,12 +190,12 @@ def test_graph_eager_and_launch_blocking_are_bitwise_identical():
 
 
 def test_reaction_forms_and_register_budgets_are_bitwise_identical():
-    """Packed FP32x2 pairs and the 85-register build compute the same bits as
-    the scalar 128-register build."""
+    """Packed FP32x2 pairs and the 80- and 64-register builds compute the
+    same bits as the scalar 128-register build."""
     w = _edge_workload(700, seed=13)
     for K in (8, 12, 16):
         a = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=1, ctas_per_sm=2))
-        for pairs, occ in ((2, 2), (1, 3), (2, 3)):
+        for pairs, occ in ((2, 2), (1, 3), (2, 3), (1, 4), (2, 4)):
             b = gpu_checkpoints(w, [350, 700], tuning=dict(nodes_per_thread=K, reaction_pairs=pairs, ctas_per_sm=occ))
             assert np.array_equal(a, b), (K, pairs, occ)
 

@@ -80,6 +80,22 @@ def test_adam_kernel_matches_the_oracle():
     assert np.max(np.abs(M.cpu().numpy() - mr)) <= 1e-6
 
 
+def test_adam_kernel_weight_average_matches_the_oracle():
+    rng = np.random.default_rng(5)
+    n = 777
+    th, m, v, g, avg = (rng.normal(size=n) for _ in range(5))
+    v = np.abs(v)
+    dt = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    T, M, Vv, G, A = dt(th), dt(m), dt(v), dt(g), dt(avg)
+    F.fibers_adam_step(T, M, Vv, G, 1e-3, 3, theta_avg=A, avg_decay=0.99)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    ref, _, _ = omlp.adam_step(f32(th), f32(m), f32(v), f32(g), 3, 1e-3)
+    ref_avg = omlp.weight_average(f32(avg), ref, 0.99)
+    assert np.max(np.abs(A.cpu().numpy() - ref_avg)) <= 1e-6
+    with pytest.raises(F.FibersError):
+        F.fibers_adam_step(T, M, Vv, G, 1e-3, 4, theta_avg=A, avg_decay=1.5)
+
+
 def test_feature_stats_kernel():
     rng = np.random.default_rng(3)
     X = rng.normal(size=(10000, 5)) * [1, 2, 3, 4, 5] + [5, 4, 3, 2, 1]
