@@ -275,7 +275,10 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
     // The reduced system is already decoupled: y_p needs D of the next
     // chunk, and this thread forms y_(p-1) itself from the previous chunk's
     // D and E with the same expression that thread evaluates, so one
-    // exchange serves both.
+    // exchange serves both.  Implicit Euler has no exchange barrier before
+    // this point, so it waits here until every thread of the fiber has read
+    // the previous solve's D and E.
+    if (s.ie) fiber_barrier(s.bar_id, s.Tw);
     x.D[s.tid] = D;
     x.E[s.tid] = E;
     fiber_barrier(s.bar_id, s.Tw);
