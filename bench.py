@@ -128,7 +128,7 @@ class ClockSampler:
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("split_step_kernel.cuh", "split_step.cu", "hh_device.cuh", "fibers_internal.h"):
+    for name in ("split_step_kernel.cuh", "split_step.cu", "hh_device.cuh", "fibers_internal.h", "solver_tables.cpp"):
         with open(os.path.join(ROOT, "paper_2107_07104_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
