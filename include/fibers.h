@@ -316,6 +316,25 @@ fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad,
  * mean, std, min, max).  Synchronises cuda_stream.  cols <= 64. */
 fib_status fibers_feature_stats(const float* X, int64_t n, int32_t cols, double* out, void* cuda_stream);
 
+/* Host-only diagnostic (no GPU needed): the coefficient tables of the
+ * partitioned tridiagonal solve that fibers_create builds for a fiber of
+ * n_nodes nodes at K nodes per thread, for the Crank-Nicolson matrix of
+ * eq:lumping_crank_nicolson_2 with r = c dt_1d / h^2 (rows (1+r, -r),
+ * (-r/2, 1+r, -r/2), (-r, 1+r)).
+ *   fp64_solve  0: the FP32 solve's PCR cutoff (2^-32); 1: the FP64 one (2^-40).
+ *   levels      out: PCR levels kept.   threads  out: threads per fiber (Tw).
+ *   rows        NULL, or 2 x K x 5 doubles: the interior chunk's row
+ *               coefficients, then the fiber's last chunk's; per row
+ *               (F1, F2, G, Ap, Bt) of the chunk elimination.
+ *   recs        NULL, or threads x (7 + 3 levels) doubles: per thread
+ *               (1/B, A/B, C/B, c0, KE, KD, KDn) of the reduced system, then
+ *               (1/b, a/b, c/b) per PCR level.
+ * Call with NULL tables first to learn levels and threads.  Errors:
+ * FIB_EINVAL (K not 4, 8, 12 or 16; n_nodes < 1 or more than 256 K; r < 0
+ * or not finite; a zero pivot). */
+fib_status fibers_solver_tables(int32_t K, double r, int32_t n_nodes, int32_t fp64_solve, int32_t* levels,
+                                int32_t* threads, double* rows, double* recs);
+
 /* Number of launches of this library's kernels enqueued so far by ctx. */
 int64_t fibers_kernel_launches(const fib_ctx* ctx);
 

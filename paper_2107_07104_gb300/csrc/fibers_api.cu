@@ -1007,6 +1007,23 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
 
 int64_t fibers_kernel_launches(const fib_ctx* c) { return c ? c->launches : 0; }
 
+fib_status fibers_solver_tables(int32_t K, double r, int32_t n_nodes, int32_t fp64_solve, int32_t* levels,
+                                int32_t* threads, double* rows, double* recs) {
+  if (K != 4 && K != 8 && K != 12 && K != 16) return fail(nullptr, FIB_EINVAL, "K must be 4, 8, 12 or 16");
+  if (n_nodes < 1 || warps_for(n_nodes, K) > kMaxWarpsPerCta)
+    return fail(nullptr, FIB_EINVAL, "n_nodes must be in [1, %d] at K = %d", 32 * kMaxWarpsPerCta * K, K);
+  if (!(r >= 0.0) || !std::isfinite(r)) return fail(nullptr, FIB_EINVAL, "r must be finite and >= 0");
+  const int32_t tw = 32 * warps_for(n_nodes, K);
+  SolverTables tab;
+  if (!build_solver_tables(K, r, {n_nodes}, {tw}, fp64_solve != 0, &tab))
+    return fail(nullptr, FIB_EINVAL, "tridiagonal tables: zero pivot (r = %g)", r);
+  if (levels) *levels = tab.levels;
+  if (threads) *threads = tw;
+  if (rows) std::copy(tab.rows.begin(), tab.rows.end(), rows);
+  if (recs) std::copy(tab.recs.begin(), tab.recs.end(), recs);
+  return FIB_OK;
+}
+
 const char* fibers_last_error(const fib_ctx* c) {
   if (!c) return g_create_error.c_str();
   return c->err.c_str();

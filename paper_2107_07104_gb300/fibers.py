@@ -37,7 +37,7 @@ EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_s
             "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
             "fibers_kernel_launches", "fibers_last_error", "fibers_destroy", "fibers_load_surrogate",
             "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward", "fibers_adam_step",
-            "fibers_feature_stats", "fibers_adaptive_stats")
+            "fibers_feature_stats", "fibers_adaptive_stats", "fibers_solver_tables")
 SUR_N_PARAMS = 17796
 SUR_BLOB_FLOATS = 3 + 5 + 5 + 4 + 4 + 5 + 5 + 5 + 5 + SUR_N_PARAMS
 SUR_WORK_PER_SAMPLE = 6 * 128 + 2 * 4
@@ -117,8 +117,9 @@ def load(build_if_missing: bool = True):
         L.fibers_mlp_forward.argtypes = [vp, i32, vp, i64, vp, vp, vp]
         L.fibers_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, f32, vp]
         L.fibers_feature_stats.argtypes = [vp, i64, i32, f64p, vp]
+        L.fibers_solver_tables.argtypes = [i32, ctypes.c_double, i32, i32, P(i32), P(i32), f64p, f64p]
         for name in ("fibers_load_surrogate", "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward",
-                     "fibers_adam_step", "fibers_feature_stats"):
+                     "fibers_adam_step", "fibers_feature_stats", "fibers_solver_tables"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
                      "fibers_write_state", "fibers_stats", "fibers_synchronize", "fibers_get_tuning",
@@ -321,6 +322,21 @@ def fibers_feature_stats(X, stream=None) -> np.ndarray:
     out = np.zeros(4 * cols)
     _check(load().fibers_feature_stats(_dev(X), n, cols, _ptr(out, ctypes.c_double), _stream_ptr(stream)), None)
     return out.reshape(cols, 4)
+
+
+def fibers_solver_tables(K: int, r: float, n_nodes: int, fp64_solve: bool = False) -> dict:
+    """Coefficient tables of the partitioned tridiagonal solve for one fiber
+    (host only): levels, threads, rows (2, K, 5) and recs (threads, 7 + 3 levels)."""
+    L = load()
+    lv, tw = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(L.fibers_solver_tables(int(K), float(r), int(n_nodes), int(bool(fp64_solve)), ctypes.byref(lv),
+                                  ctypes.byref(tw), None, None), None)
+    rows = np.zeros(2 * K * 5)
+    recs = np.zeros(tw.value * (7 + 3 * lv.value))
+    _check(L.fibers_solver_tables(int(K), float(r), int(n_nodes), int(bool(fp64_solve)), None, None,
+                                  _ptr(rows, ctypes.c_double), _ptr(recs, ctypes.c_double)), None)
+    return dict(levels=lv.value, threads=tw.value, rows=rows.reshape(2, K, 5),
+                recs=recs.reshape(tw.value, 7 + 3 * lv.value))
 
 
 def fibers_kernel_launches(ctx) -> int:
