@@ -191,9 +191,11 @@ fib_status validate(const fib_params* p) {
 
 // ---- layout ---------------------------------------------------------------
 
+// Warps a fiber of n nodes needs at K nodes per thread (64-bit, so that no
+// int32 length can wrap it below the limit checks).
 int warps_for(int32_t n, int K) {
-  const int T = (n + K - 1) / K;
-  return (T + 31) / 32;
+  const int64_t T = ((int64_t)n + K - 1) / K;
+  return (int)std::min<int64_t>((T + 31) / 32, INT32_MAX);
 }
 
 int auto_K(const std::vector<int32_t>& n_nodes) {

@@ -151,8 +151,8 @@ def test_dropping_the_kept_levels_breaks_the_solve():
     assert err > 1e-3
 
 
-@pytest.mark.parametrize("args", [(5, 0.1, 100, 0), (8, 0.1, 0, 0), (8, 0.1, 2049, 0), (8, -1.0, 10, 0),
-                                  (8, float("nan"), 10, 0), (8, float("inf"), 10, 1)])
+@pytest.mark.parametrize("args", [(5, 0.1, 100, 0), (8, 0.1, 0, 0), (8, 0.1, 2049, 0), (16, 0.1, 2**31 - 1, 0),
+                                  (8, -1.0, 10, 0), (8, float("nan"), 10, 0), (8, float("inf"), 10, 1)])
 def test_solver_tables_reject_bad_arguments(args):
     with pytest.raises(F.FibersError) as ei:
         F.fibers_solver_tables(*args)
