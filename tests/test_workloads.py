@@ -48,3 +48,17 @@ def test_subset_keeps_fibers_and_initial_voltages():
     off = w.offsets()
     assert np.array_equal(s.n_nodes, w.n_nodes[[1, 5, 7]])
     assert np.array_equal(s.vm0, np.concatenate([w.vm0[off[i]:off[i + 1]] for i in (1, 5, 7)]))
+
+
+def test_full_scale_bundle_recipe():
+    w = W.bundle_67600(seed=5, t_end_ms=100.0)
+    assert w.n_fibers == 67600 and np.all(w.n_nodes == 1481) and w.n_mu == 200
+    assert w.total_nodes == 100_115_600 and w.n_steps == 33334  # ceil(100 / 0.003)
+    counts = np.bincount(w.mu_of_fiber, minlength=200)
+    assert counts.min() >= 1
+    q = W.mu_size_probabilities(200, 10.0 ** (1.0 / 200))
+    assert abs(q[-1] / q[0] - 10.0 ** (199 / 200)) < 1e-9  # largest/smallest MU about 10
+    assert np.corrcoef(counts, q * 67600)[0, 1] > 0.95
+    # rates uniform in 10-30 Hz: about 2 firings per MU in 100 ms
+    assert 1.5 < np.diff(w.mu_offsets).mean() < 2.5
+    assert np.all(np.abs(w.junction - 740) <= 74)
