@@ -199,7 +199,7 @@ int warps_for(int32_t n, int K) {
 }
 
 int auto_K(const std::vector<int32_t>& n_nodes) {
-  // K = 8 (measured fastest on GB300 with packed pairs and the 85-register
+  // K = 8 (measured fastest on GB300 with packed pairs and the 80-register
   // budget) whenever every fiber fits; otherwise the fewest padded nodes
   int max_n = 0;
   for (int32_t n : n_nodes) max_n = std::max(max_n, n);
