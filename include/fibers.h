@@ -196,11 +196,16 @@ fib_status read_vm(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_dev
  * cudaMalloc, cudaFree or allocating routine.
  *   host_out  host buffer for V (mV, float, ragged order), capacity >= sum(n_nodes).
  * Limit: at most 2,097,152 nodes per context (the array's size); larger
- * contexts get FIB_EINVAL and should use read_vm.  The first call on a GPU
- * looks up the array's device address on that GPU (cudaGetSymbolAddress);
- * make that first call before any stream capture begins.  All calls share
- * the array and it keeps the last call's contents; calls that overlap on
- * the GPU (two contexts reading on different streams at once) race on it.
+ * contexts get FIB_EINVAL and should use read_vm.  The array's device
+ * memory is reserved, and its device address looked up
+ * (cudaGetSymbolAddress), by fibers_create on the context's GPU, so the
+ * first read_vm_static call does not reserve it even under CUDA's lazy
+ * module loading.  Only if that look-up failed at creation does the first
+ * call on a GPU try again, and it may then reserve the array; make such a
+ * call before any stream capture begins.  All calls share the array and it
+ * keeps the last call's contents; calls that overlap on the GPU (two
+ * contexts reading on different streams at once) race on it.  The calling
+ * thread's current device is the same after the call as before it.
  * Synchronises the context's stream.  Errors as read_vm. */
 fib_status read_vm_static(fib_ctx* ctx, float* host_out, size_t capacity);
 
@@ -208,36 +213,54 @@ fib_status read_vm_static(fib_ctx* ctx, float* host_out, size_t capacity);
  * of sum(n_nodes) floats in ragged order, u | m | h | n, where u = V - Vrest
  * is the depolarisation in mV (the form the library integrates; V itself is
  * u + Vrest) and m, h, n are the HH gates.  The copy is bit-exact, so it can
- * serve as a checkpoint.  Synchronises.  Same errors as read_vm. */
+ * serve as a checkpoint.  Synchronises.  Same errors as read_vm.
+ * Thesis: the state vector y = (V, m, h, n) of every model instance
+ * (eq:subcellular); the thesis copies back only the subset needed for
+ * output (section "Code Generation for GPUs") and has no checkpoint call. */
 fib_status fibers_read_state(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
 
 /* Replaces the full state with in (layout of fibers_read_state: u | m | h |
  * n) and sets the index of the next split step to step_index (>= 0).  Used
  * for checkpoint / resume: k steps, read_state, write_state, n - k steps
  * gives bit-for-bit the same state as n steps.  Clears a pending non-finite
- * flag. */
+ * flag, and in surrogate mode empties the network-node lists.  The thesis
+ * has no counterpart (its initial state is sent to the GPU once, section
+ * "Code Generation for GPUs"); this call exists for resuming runs.
+ * Errors: FIB_EINVAL (count != 4 sum(n_nodes), step_index < 0), FIB_ECUDA. */
 fib_status fibers_write_state(fib_ctx* ctx, const float* in, size_t count, int32_t in_is_device,
                               int64_t step_index);
 
 /* Index of the next split step, and nodes handled by the fallback path in
- * surrogate mode (0 otherwise).  Synchronises. */
+ * surrogate mode (0 otherwise).  Synchronises.  No thesis counterpart (a
+ * diagnostic of this library); errors as fibers_synchronize. */
 fib_status fibers_stats(fib_ctx* ctx, int64_t* steps_done, int64_t* fallback_nodes);
 
 /* Fiber-steps the adaptive scheme skipped so far (0 without
- * FIB_FLAG_ADAPTIVE).  Synchronises. */
+ * FIB_FLAG_ADAPTIVE).  Synchronises.  Thesis: the points in equilibrium
+ * that adaptive computation leaves out (sec:adaptive_computation_for_fiber_based). */
 fib_status fibers_adaptive_stats(fib_ctx* ctx, int64_t* skipped_fiber_steps);
 
-/* Waits for all enqueued work and reports device-side errors. */
+/* Waits for all enqueued work and reports device-side errors: FIB_ENONFINITE
+ * (state became NaN/Inf), FIB_ESTATE (surrogate node list overflowed),
+ * FIB_ECUDA.  Thesis: the point of synchronisation between blocks of GPU
+ * timesteps (section "Code Generation for GPUs"). */
 fib_status fibers_synchronize(fib_ctx* ctx);
 
-/* Reads / changes the launch shape.  Changing it keeps the state. */
+/* Reads / changes the launch shape.  Changing it keeps the state.  The
+ * thesis has no counterpart: it distributes whole fibers to processes for
+ * load balance (sec:partitioning_requirements), while here fibers are packed
+ * into thread blocks by the layout these values choose.  Errors: FIB_EINVAL
+ * (a value out of range, fibers too long for the shape; the old shape stays),
+ * FIB_ENOMEM, FIB_ECUDA. */
 fib_status fibers_get_tuning(const fib_ctx* ctx, fib_tuning* out);
 fib_status fibers_set_tuning(fib_ctx* ctx, const fib_tuning* tuning);
 
 /* Times candidate launch shapes on this context's own fibers for n_trial_steps
- * split steps each, keeps the fastest, and restores the state and step index
- * so the simulation is unchanged.  best (nullable) receives the choice.
- * Synchronises. */
+ * split steps each, keeps the fastest, and restores the state, step index and
+ * adaptive skip count so the simulation is unchanged.  best (nullable)
+ * receives the choice.  Synchronises.  No thesis counterpart (see
+ * fibers_set_tuning).  Errors: FIB_EINVAL (n_trial_steps < 1), FIB_ENOTSUP
+ * (surrogate mode, whose step kernel it does not time), FIB_ECUDA. */
 fib_status fibers_autotune(fib_ctx* ctx, int32_t n_trial_steps, fib_tuning* best);
 
 /* ---------------------------------------------------------------------------
@@ -335,14 +358,17 @@ fib_status fibers_feature_stats(const float* X, int64_t n, int32_t cols, double*
 fib_status fibers_solver_tables(int32_t K, double r, int32_t n_nodes, int32_t fp64_solve, int32_t* levels,
                                 int32_t* threads, double* rows, double* recs);
 
-/* Number of launches of this library's kernels enqueued so far by ctx. */
+/* Number of launches of this library's kernels enqueued so far by ctx (a
+ * diagnostic of this library, no thesis counterpart; 0 for ctx == NULL). */
 int64_t fibers_kernel_launches(const fib_ctx* ctx);
 
 /* Message of the last failing call on ctx (never NULL).  With ctx == NULL:
- * the message of the last failed fibers_create on this thread. */
+ * the message of the last failed fibers_create on this thread.  No thesis
+ * counterpart. */
 const char* fibers_last_error(const fib_ctx* ctx);
 
-/* Frees everything the context owns.  NULL is allowed. */
+/* Frees everything the context owns, after waiting for its stream.  NULL is
+ * allowed.  No thesis counterpart. */
 void fibers_destroy(fib_ctx* ctx);
 
 #ifdef __cplusplus

@@ -494,7 +494,16 @@ fib_status build_graph(fib_ctx* c) {
 fib_status check_flag(fib_ctx* c) {
   int32_t flag = 0;
   CU(c, cudaMemcpy(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  if (flag & 2) return fail(c, FIB_ESTATE, "surrogate network-node list overflowed; its entries were dropped");
   if (flag & 1) return fail(c, FIB_ENONFINITE, "state became non-finite (NaN/Inf)");
+  return FIB_OK;
+}
+
+// Surrogate mode: the network-node list counters of both step parities
+// start at zero.  Needed wherever the step index is set, since the network
+// pass empties only the other parity's list for the next step.
+fib_status reset_sur_lists(fib_ctx* c) {
+  if (c->d_sur_count) CU(c, cudaMemsetAsync(c->d_sur_count, 0, 2 * sizeof(unsigned int), c->stream));
   return FIB_OK;
 }
 
@@ -679,6 +688,9 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
   cudaError_t e = cudaGetDevice(&cx->device);
   if (e != cudaSuccess) return fail(nullptr, FIB_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   cx->stream = static_cast<cudaStream_t>(cuda_stream);
+  // Reserve read_vm_static's staging array on this device now (a failure
+  // here is not an error of this call: read_vm_static tries again).
+  if (fib::prepare_static_stage(cx->device) != 0) cudaGetLastError();
   fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000, 0, 0};
   st = build_layout(cx, t);
   if (st == FIB_OK) {
@@ -858,6 +870,8 @@ fib_status fibers_write_state(fib_ctx* c, const float* in, size_t count, int32_t
   }
   CU(c, cudaMemcpyAsync(c->d_step, &step_index, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   CU(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream));
+  fib_status st = reset_sur_lists(c);
+  if (st != FIB_OK) return st;
   CU(c, cudaStreamSynchronize(c->stream));
   c->next_step = step_index;
   return FIB_OK;
@@ -939,9 +953,16 @@ fib_status fibers_set_tuning(fib_ctx* c, const fib_tuning* t) {
 fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) {
   if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
   if (n_trial_steps < 1) return fail(c, FIB_EINVAL, "n_trial_steps must be >= 1");
+  if (c->p.mode == FIB_MODE_SURROGATE)
+    return fail(c, FIB_ENOTSUP, "autotune times the plain step kernel, which surrogate mode does not run");
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
   const size_t need = 4 * (size_t)c->total;
   const int64_t step_keep = c->next_step;
+  // the trial launches of adaptive mode count skipped fiber-steps; keep the
+  // context's own count
+  unsigned long long skipped_keep = 0;
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (c->d_skipped) CU(c, cudaMemcpy(&skipped_keep, c->d_skipped, sizeof(skipped_keep), cudaMemcpyDeviceToHost));
   float* keep = nullptr;
   if (need > 0) {
     CU(c, cudaMalloc(&keep, sizeof(float) * need));
@@ -997,6 +1018,8 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
   if (result == FIB_OK) {
     cudaMemcpyAsync(c->d_step, &step_keep, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
     cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream);
+    if (c->d_skipped)
+      cudaMemcpyAsync(c->d_skipped, &skipped_keep, sizeof(skipped_keep), cudaMemcpyHostToDevice, c->stream);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) result = fail(c, FIB_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
   }

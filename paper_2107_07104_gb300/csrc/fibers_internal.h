@@ -64,7 +64,7 @@ struct StepArgs {
   const int64_t* mu_off;   // [n_mu + 1]
   const int64_t* fire_k;   // firing substep index, sorted within each MU
   const int64_t* step_base;  // device-resident index of the next split step
-  int32_t* flag;           // bit 0: non-finite state seen
+  int32_t* flag;           // bit 0: non-finite state seen; bit 1: surrogate node list overflowed
   HHConst hh;
   double r;                // tridiagonal-table parameter: c dt_1d / h^2 (CN), 2 c dt_1d / h^2 (IE)
   int64_t step_offset;     // this launch starts at *step_base + step_offset
@@ -162,4 +162,8 @@ struct CtxView {
 };
 fib_status ctx_view(fib_ctx* c, CtxView* out);
 fib_status ctx_fail(fib_ctx* c, fib_status s, const char* msg);
+// Looks up read_vm_static's staging array on `device` (which must be
+// current), loading its module and so reserving the array now rather than
+// inside the first read_vm_static call.  Returns a cudaError_t.
+int prepare_static_stage(int device);
 }  // namespace fib

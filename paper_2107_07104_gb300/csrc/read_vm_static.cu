@@ -15,6 +15,14 @@
 // contents; nothing in it needs to start at zero because each call overwrites
 // every element it copies out.  Calls that overlap on the GPU (for example two
 // contexts reading on different streams at the same time) race on the array.
+//
+// With CUDA's lazy module loading (the default), the device memory of this
+// file's module, the 8 MiB array included, is reserved when the module is
+// first used.  fibers_create therefore looks the address up on its device
+// (prepare_static_stage), so the reservation happens there, where allocating
+// is expected, and not inside the first read_vm_static call.  If that
+// look-up failed at creation, the first read_vm_static call on the device
+// tries again, and then it may reserve the array itself.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -55,7 +63,24 @@ cudaError_t stage_address(int device, float** out) {
   return cudaSuccess;
 }
 
+// Restores the calling thread's current device when the call returns.
+struct DeviceGuard {
+  int saved = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&saved) != cudaSuccess) saved = -1;
+  }
+  ~DeviceGuard() {
+    if (saved >= 0) cudaSetDevice(saved);
+  }
+};
+
 }  // namespace
+
+int fib::prepare_static_stage(int device) {
+  if (device < 0 || device >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+  float* p = nullptr;
+  return (int)stage_address(device, &p);
+}
 
 extern "C" fib_status read_vm_static(fib_ctx* ctx, float* host_out, size_t capacity) {
   fib::CtxView v;
@@ -68,6 +93,7 @@ extern "C" fib_status read_vm_static(fib_ctx* ctx, float* host_out, size_t capac
   if (capacity < (size_t)v.total) return fib::ctx_fail(ctx, FIB_EINVAL, "capacity is smaller than the node count");
   if (v.total > 0 && !host_out) return fib::ctx_fail(ctx, FIB_EINVAL, "host_out is NULL");
   if (v.device < 0 || v.device >= kMaxDevices) return fib::ctx_fail(ctx, FIB_ENOTSUP, "device index out of range");
+  const DeviceGuard keep_device;
   cudaError_t e = cudaSetDevice(v.device);
   if (e != cudaSuccess) return fib::ctx_fail(ctx, FIB_ECUDA, cudaGetErrorString(e));
   float* stage = nullptr;

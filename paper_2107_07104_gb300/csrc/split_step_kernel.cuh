@@ -369,6 +369,14 @@ __device__ __forceinline__ void list_network_nodes(const StepArgs& a, const floa
   unsigned int first = 0;
   if (lane == 31) first = atomicAdd(a.sur_count + (stp & 1), (unsigned int)incl);
   first = __shfl_sync(0xffffffffu, first, 31);
+  const unsigned int warp_total = (unsigned int)__shfl_sync(0xffffffffu, incl, 31);
+  // A node is listed at most once per step, so the list cannot outgrow
+  // sur_cap unless its counter was left stale; then nothing is stored and
+  // the host reports the overflow.
+  if ((unsigned long long)first + warp_total > (unsigned long long)a.sur_cap) {
+    if (lane == 31) atomicOr(a.flag, 2);
+    return;
+  }
   unsigned int pos = first + (unsigned int)(incl - cnt);
   float* L = a.sur_list + (stp & 1) * 6 * a.sur_cap;
 #pragma unroll

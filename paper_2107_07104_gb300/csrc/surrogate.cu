@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
   float* stage = sB + 2 * kHid + 8;
   const int64_t stp = *a.step_base + a.step_offset;
   const int par = (int)(stp & 1);
-  const int64_t count = a.list_count[par];
+  const int64_t listed = a.list_count[par];
+  const int64_t count = listed < a.list_cap ? listed : a.list_cap;  // overflow is flagged by the step kernel
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.list_count[par ^ 1] = 0;
     atomicAdd(a.fallback_count, (unsigned long long)(a.real_nodes - count));

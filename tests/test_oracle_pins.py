@@ -93,6 +93,50 @@ def test_gate_rhs_sign_and_rates_singularities():
     assert np.all(f2[1:] > 0)
 
 
+def _hh_equilibrium_max_real_eig(p, current):
+    """Largest real part of the eigenvalues of the oracle's HH right-hand side
+    linearised at its equilibrium under a constant applied current: the
+    equilibrium V solves dV/dt = 0 with the gates at their steady states, and
+    the Jacobian is taken by central differences of the oracle's RHS."""
+    from scipy.optimize import brentq
+
+    def dvdt(V):
+        return oracle.hh_rhs(p, np.array([V, *oracle.gates_inf(p, V)]), current)[0]
+
+    Vs = np.linspace(p["Vrest"] - 20.0, p["Vrest"] + 60.0, 321)
+    fs = np.array([dvdt(v) for v in Vs])
+    roots = np.nonzero(fs[:-1] * fs[1:] < 0)[0]
+    assert roots.size == 1  # the HH equilibrium is unique for every current
+    V = brentq(dvdt, Vs[roots[0]], Vs[roots[0] + 1], xtol=1e-13)
+    y = np.array([V, *oracle.gates_inf(p, V)])
+    J = np.zeros((4, 4))
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = 1e-6
+        J[:, k] = (oracle.hh_rhs(p, y + e, current) - oracle.hh_rhs(p, y - e, current)) / 2e-6
+    return float(np.max(np.linalg.eigvals(J).real))
+
+
+def test_hh_rates_away_from_rest_give_the_published_hopf_currents():
+    # Linear stability of the space-clamped HH model: the equilibrium loses
+    # stability at I = 9.78 and regains it at 154.5 uA/cm^2 (Hassard 1978;
+    # Rinzel & Miller 1980).  The equilibrium sits at 5.3 and 22 mV above
+    # rest there, so these currents depend on every rate's value and slope
+    # away from rest: a wrong exponent scale (/18 -> /20 in beta_m, /80 -> /70
+    # in beta_n), offset or prefactor in any of the six rates moves at least
+    # one of them by more than 4 %.
+    from scipy.optimize import brentq
+    g = golden("hh_hopf_points.txt")
+    p = P(EL=-75.0 + 10.613)
+    lower = brentq(lambda I: _hh_equilibrium_max_real_eig(p, I), 5.0, 15.0, xtol=1e-9)
+    upper = brentq(lambda I: _hh_equilibrium_max_real_eig(p, I), 100.0, 200.0, xtol=1e-9)
+    assert abs(lower - g["hopf_lower_uA_per_cm2"]) <= 0.01   # published to 3 digits
+    assert abs(upper - g["hopf_upper_uA_per_cm2"]) <= 0.1    # published to 4 digits
+    # between them the equilibrium is unstable, outside stable
+    assert _hh_equilibrium_max_real_eig(p, 50.0) > 0
+    assert _hh_equilibrium_max_real_eig(p, 5.0) < 0 and _hh_equilibrium_max_real_eig(p, 200.0) < 0
+
+
 def test_ap_shape_matches_thesis_facts():
     facts = golden("thesis_ap_facts.txt")
     w = W.single_fiber(t_end_ms=35.0, n_nodes=201)

@@ -207,3 +207,28 @@ def test_surrogate_mode_graphs_match_eager_launches():
     assert out[0][1] < 600 * w.total_nodes  # the network did handle nodes
     for st, fb in out[1:]:
         assert np.array_equal(st, out[0][0]) and fb == out[0][1]
+
+
+def test_surrogate_rewind_matches_a_fresh_context():
+    """Rewinding a surrogate context (write_state) empties the network-node
+    lists: after 121 steps the list of step 120's parity is full of nodes in
+    mid action potential; restoring the initial state at step 0 (the same
+    parity) and stepping on gives the same bits as a fresh context."""
+    w = W.small_ragged(seed=34, n_fibers=30, lo=300, hi=1200, n_steps=300)
+    w.mu_offsets = np.arange(4, dtype=np.int64)
+    w.fire_times = np.array([0.0, 0.05, 0.1])
+    blob = S.load_blob()
+    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as f:
+        F.fibers_load_surrogate(f.ctx, blob)
+        st0 = f.read_state()
+        f.step(121)                 # steps 0..120: the last one (even) lists many nodes
+        _, fb_run = f.stats()
+        f.write_state(st0, 0)       # rewind to step 0 (even)
+        f.step(40)
+        got = f.read_state()
+    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as g:
+        F.fibers_load_surrogate(g.ctx, blob)
+        g.step(40)
+        ref = g.read_state()
+    assert fb_run < 121 * w.total_nodes  # the network handled nodes before the rewind
+    assert np.array_equal(got, ref)
