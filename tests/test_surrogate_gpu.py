@@ -215,8 +215,8 @@ def test_surrogate_rewind_matches_a_fresh_context():
     mid action potential; restoring the initial state at step 0 (the same
     parity) and stepping on gives the same bits as a fresh context."""
     w = W.small_ragged(seed=34, n_fibers=30, lo=300, hi=1200, n_steps=300)
-    w.mu_offsets = np.arange(4, dtype=np.int64)
-    w.fire_times = np.array([0.0, 0.05, 0.1])
+    w.mu_offsets = np.arange(5, dtype=np.int64)           # one firing per motor unit
+    w.fire_times = np.array([0.0, 0.05, 0.1, 0.15])
     blob = S.load_blob()
     with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as f:
         F.fibers_load_surrogate(f.ctx, blob)
