@@ -1,21 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark: fiber node-updates/s of the full Strang split step on GB300.
 
-Workload (per GPU): the 7744-fiber bundle (88 x 88 fibers x 1481 nodes,
-h = 0.01 cm, 100 motor units with exponential sizes, Poisson firing at
-10-30 Hz), seeded synthetic inputs.  One benchmark "step" is one split step
-(CN half, 3 Heun substeps, CN half) of every fiber.  The timed region runs
---steps split steps through the library's CUDA-graph step loop with the state
-already resident in HBM.
+Workload (per GPU): the full-scale bundle, 67,600 fibers (260 x 260) x 1481
+nodes = 1.0e8 nodes, h = 0.01 cm, 200 motor units with exponential sizes,
+Poisson firing at 10-30 Hz; seeded synthetic inputs.  One benchmark "step" is
+one CUDA-graph launch of BENCH_SPLIT_STEPS = 100 split steps (each: CN half,
+3 Heun substeps, CN half, for every fiber), i.e. 0.3 ms of simulated time.
+The timed region runs --steps such graph launches with the state already
+resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank simulates its own bundle (seed 2 + rank) on
+Under torchrun (N > 1) every rank simulates its own bundle (seed 5 + rank) on
 its own GPU with no data-path communication (fibers are independent): weak
 scaling, whole-job value = sum of node-updates over ranks / max time.
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference
 implementation of this method) on the host cores instead.
+
+Secondary legs on the same GPU (each optional): the 7744-fiber bundle, the
+ragged 20,000-fiber bundle with the autotuner and 1000-step graphs, the
+learned-surrogate path timed while action potentials propagate, adaptive
+computation, the scheme variants and the exp* approximation.
 """
 from __future__ import annotations
 
@@ -38,7 +44,8 @@ from paper_2107_07104_gb300 import workloads as W  # noqa: E402
 
 METRIC = "fiber node-updates/s (full split step) at max|ΔVm|≤0.5 mV, plain FP32 vs surrogate"
 UNIT = "node-updates/s"
-WORKLOAD = "bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz"
+WORKLOAD = "bundle 67600 fibers x 1481 nodes (260x260), 200 MUs, Poisson 10-30 Hz"
+BENCH_SPLIT_STEPS = 100          # split steps per benchmark step (one CUDA-graph launch)
 # Algorithmic work per node-update of the plain FP32 path (the method's operation counts):
 BYTES_PER_NODE_UPDATE = 32.0     # read + write V, m, h, n (FP32) once per split step
 FMA_OPS_PER_NODE_UPDATE = 238.0  # FP32 FMA-pipe operations of the method per split step
@@ -49,6 +56,7 @@ RCP_OPS_PER_NODE_UPDATE = 18.0   # 1/x special-function operations per split ste
 FP32_LANES_PER_SM = 128.0
 EX2_PER_SM = 32.0
 RCP_PER_SM = 16.0
+NCU_SUMMARY = os.path.join("profiles", "split_step_kernel_bundle7744_ncu.md")
 
 
 def _env_int(k, d):
@@ -74,8 +82,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
         self.gpu = gpu_index
+        self.period = period_ms
         self.proc = None
         self.path = None
 
@@ -85,8 +94,9 @@ class ClockSampler:
             os.close(fd)
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period)],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)  # let the sampler start before the timed region
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -103,7 +113,7 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not self.path:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
+        sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -113,6 +123,7 @@ class ClockSampler:
                 try:
                     sm.append(float(parts[1]))
                     smax.append(float(parts[2]))
+                    pw.append(float(parts[3]))
                 except ValueError:
                     continue
                 for name, v in zip(names, parts[5:9]):
@@ -122,7 +133,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sample_period_ms": self.period, "power_w_max": max(pw) if pw else None}
 
 
 def kernel_source_hash() -> str:
@@ -134,35 +145,43 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def dram_traffic_from_profile(tune):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when the kernel source or the launch shape changed since."""
-    path = os.path.join(ROOT, "profiles", "split_step_kernel_bundle7744_ncu.md")
+def profile_fields():
+    """Capture identity and DRAM figures of the committed ncu summary."""
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, NCU_SUMMARY)) as f:
             text = f.read()
     except OSError:
-        return None
+        return {}
     fields = {}
     for line in text.splitlines():
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             fields[k.strip()] = v.strip().strip("`")
+    return fields
+
+
+def dram_traffic_per_node_update(tune):
+    """DRAM bytes per node-update of the step kernel from the committed ncu
+    capture, or None when the kernel source or the launch shape has changed
+    since the counters were taken."""
+    fields = profile_fields()
     try:
         same = (fields.get("kernel source sha256[:16]") == kernel_source_hash()
                 and int(fields.get("steps_per_launch", -1)) == tune["steps_per_launch"]
                 and int(fields.get("nodes_per_thread", -1)) == tune["nodes_per_thread"]
                 and int(fields.get("reaction_pairs", -1)) == tune["reaction_pairs"]
                 and int(fields.get("ctas_per_sm", -1)) == tune["ctas_per_sm"])
-        return float(fields["dram bytes per launch"]) if same else None
+        if not same:
+            return None
+        return float(fields["dram bytes per launch"]) / float(fields["node-updates per launch"])
     except (KeyError, ValueError):
         return None
 
 
 def rank_workload(rank: int):
-    """Each rank simulates its own seeded 7744-fiber bundle: fibers are
+    """Each rank simulates its own seeded full-scale bundle: fibers are
     independent, so ranks share nothing on the data path (weak scaling)."""
-    return W.bundle_7744(seed=2 + rank, t_end_ms=20.0)
+    return W.bundle_67600(seed=5 + rank, t_end_ms=100.0)
 
 
 def aggregate_over_ranks(node_updates_local: float, seconds_local: float, dist, device=None):
@@ -222,7 +241,7 @@ def accuracy_vs_oracle(tune, steps):
     bench's launch shape) against the FP64 oracle's final V."""
     from paper_2107_07104_gb300 import fibers as F
     sub, v_ref = oracle_rate.last
-    with F.Fibers.from_workload(sub, tuning=tune) as f:
+    with F.Fibers.from_workload(sub, tuning=dict(tune, graph_steps=0)) as f:
         f.step(steps)
         v = f.read_vm().astype(np.float64)
     d = v - v_ref
@@ -234,12 +253,13 @@ def accuracy_vs_oracle(tune, steps):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    w = W.bundle_7744(seed=2, t_end_ms=20.0)
+    w = rank_workload(0)
     import oracle
     cores = cpu_cores()
     # size the per-step sample so that warm-up + timed steps take about 100 s
     rate, _, _, _ = oracle_rate(w, 64, 2)
-    fibers = int(np.clip(rate * 100.0 / (1481.0 * (args.steps + args.warmup)), 16, 1024))
+    split = args.steps + args.warmup
+    fibers = int(np.clip(rate * 100.0 / (1481.0 * split), 16, 1024))
     sub = w.subset(np.arange(fibers))
     state = oracle.init_state(sub.params, sub.total_nodes, sub.vm0)
     step = 0
@@ -252,7 +272,8 @@ def run_reference(args, world, rank):
                args.steps, n_threads=cores)
     dt = time.perf_counter() - t0
     value = sub.total_nodes * args.steps / dt
-    sample = f"first {fibers} of 7744 fibers x 1481 nodes, {args.steps} split steps, FP64 oracle"
+    sample = (f"first {fibers} of 67600 fibers x 1481 nodes, one split step per benchmark step "
+              f"({args.steps} timed), FP64 oracle")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -263,6 +284,21 @@ def run_reference(args, world, rank):
     return 0
 
 
+def timed_graph_launches(fib, stream, dev, k, split_steps):
+    """k benchmark steps (each `split_steps` split steps, one graph launch) with
+    a CUDA event between launches on the launching stream: (total ms, per-launch ms)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    for i in range(k):
+        fib.step(split_steps)
+        ev[i + 1].record(stream)
+    ev[k].synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(k)]
+    return ev[0].elapsed_time(ev[k]), per
+
+
 def run_gpu(args, world, rank, local, dist):
     import torch
     from paper_2107_07104_gb300 import fibers as F
@@ -271,65 +307,55 @@ def run_gpu(args, world, rank, local, dist):
     dev = torch.device("cuda", local)
     w = rank_workload(rank)
     total = w.total_nodes
+    S = BENCH_SPLIT_STEPS
     stream = torch.cuda.Stream(device=dev)
     tuning = dict(nodes_per_thread=args.nodes_per_thread, warps_per_cta=args.warps_per_cta,
-                  steps_per_launch=args.steps_per_launch, graph_steps=args.graph_steps,
-                  reaction_pairs=args.reaction_pairs, ctas_per_sm=args.ctas_per_sm)
+                  steps_per_launch=S, graph_steps=S, reaction_pairs=args.reaction_pairs,
+                  ctas_per_sm=args.ctas_per_sm)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # ---- device-resident timing: K split steps, state already in HBM --------
+    # ---- device-resident timing: K graph launches, state already in HBM ----
     fib = F.Fibers.from_workload(w, tuning=tuning, stream=stream)
-    if args.autotune:
-        fib.autotune(20)
-    fib.step(args.warmup)
+    for _ in range(args.warmup):
+        fib.step(S)
     fib.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     launches0 = fib.kernel_launches
     barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        e0.record(stream)
-        fib.step(args.steps)
-        e1.record(stream)
-        e1.synchronize()
+        ms, per_launch = timed_graph_launches(fib, stream, dev, args.steps, S)
     torch.cuda.synchronize(dev)
     barrier()
-    ms = e0.elapsed_time(e1)
     launches = fib.kernel_launches - launches0
     tune = fib.tuning
     vm = fib.read_vm()
     finite = bool(np.isfinite(vm).all())
     fib.close()
-    S = tune["steps_per_launch"]
-    G = tune["graph_steps"]
-    split_launches = 0
-    rem = args.steps
-    if G > 0:
-        split_launches += (rem // G) * ((G + S - 1) // S)
-        rem %= G
-    split_launches += (rem + S - 1) // S
-
-    node_updates, t_max = aggregate_over_ranks(float(total) * args.steps, ms / 1e3, dist, dev)
+    split_steps = args.steps * S
+    node_updates, t_max = aggregate_over_ranks(float(total) * split_steps, ms / 1e3, dist, dev)
     value = node_updates / t_max
 
     # ---- end to end through the C ABI with host buffers ---------------------
-    host_out = np.empty(total, np.float32)
+    # Timed: fibers_create and set_stimulus_times from host arrays (the
+    # bundle's inputs), then every benchmark step one graph launch of S split
+    # steps and read_vm of V into pinned host memory.
+    host_out = torch.empty(total, dtype=torch.float32, pin_memory=True)
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     fib2 = F.Fibers.from_workload(w, tuning=tune, stream=stream)
-    fib2.step(args.steps)
-    fib2.read_vm(host_out)
+    for _ in range(args.steps):
+        fib2.step(S)
+        F.read_vm(fib2.ctx, host_out)
     t_e2e = time.perf_counter() - t0
     fib2.close()
-    _, te = aggregate_over_ranks(float(total) * args.steps, t_e2e, dist, dev)
+    _, te = aggregate_over_ranks(float(total) * split_steps, t_e2e, dist, dev)
     e2e_value = node_updates / te
     h2d = 12 * w.n_fibers + 8 * (w.mu_offsets.size + w.fire_times.size)
-    d2h = 4 * total
+    d2h = 4 * total * args.steps
 
     if rank != 0:
         return 0
@@ -337,64 +363,83 @@ def run_gpu(args, world, rank, local, dist):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    per_gpu_rate = float(total) * args.steps / (ms / 1e3)
+    per_gpu_rate = float(total) * split_steps / (ms / 1e3)
+    clocks = clk.summary()
+    # The dominant kernel: one split-step launch per graph (the graph's other
+    # kernel is the 1-thread step-counter update).  Per-launch duration from
+    # the events between graph launches.
+    launch_ms = statistics.mean(per_launch)
+    alg_bytes = BYTES_PER_NODE_UPDATE * total * S
+    achieved_gbs = alg_bytes / (launch_ms * 1e-3) / 1e9
+    traffic_per_nu = dram_traffic_per_node_update(tune)
     # ALU roofline: node-updates/s if the binding pipe (FP32 FMA or the
     # special-function XU pipe) ran at its full rate on every SM at the
     # maximum SM clock.
     fma_clk = FMA_OPS_PER_NODE_UPDATE / FP32_LANES_PER_SM
     xu_clk = EX2_OPS_PER_NODE_UPDATE / EX2_PER_SM + RCP_OPS_PER_NODE_UPDATE / RCP_PER_SM
     alu_peak = n_sm * sm_max / max(fma_clk, xu_clk)
-    kernel_ms = ms / max(split_launches, 1)
-    traffic = dram_traffic_from_profile(tune)
     cpu = None
+    accuracy = None
     if not args.no_cpu_baseline:
         rate, dt, cores, nodes = oracle_rate(w, args.cpu_fibers, args.cpu_steps)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_fibers} of 7744 fibers x 1481 nodes, {args.cpu_steps} split steps "
+               "sample": f"first {args.cpu_fibers} of 67600 fibers x 1481 nodes, {args.cpu_steps} split steps "
                          f"({dt:.1f} s of FP64 oracle on {cores} threads)"}
         accuracy = accuracy_vs_oracle(tune, args.cpu_steps)
-    else:
-        accuracy = None
-    clocks = clk.summary()
-    sur = None if args.no_surrogate else surrogate_leg(args, w, tune, stream, dev, total, per_gpu_rate)
-    adaptive = None if args.no_adaptive else adaptive_leg(args, w, tune, stream, dev, total, per_gpu_rate)
-    schemes = None if args.no_schemes else schemes_leg(args, w, tune, stream, dev, total)
-    expapx = None if args.no_exp_approx else exp_approx_leg(args, w, tune, stream, dev, total, per_gpu_rate)
-    full = None if args.no_full_scale else full_scale_leg(stream, dev)
+    legs = {}
+    if not args.no_legs:
+        legs["bundle_7744"] = bundle_7744_leg(args, stream, dev)
+        legs["ragged_20000"] = ragged_leg(args, stream, dev)
+        if not args.no_surrogate:
+            legs["surrogate"] = surrogate_leg(args, stream, dev)
+        legs["adaptive"] = adaptive_leg(args, stream, dev)
+        legs["schemes"] = schemes_leg(args, stream, dev)
+        legs["exp_approx"] = exp_approx_leg(args, stream, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fibers": int(w.n_fibers), "nodes": int(total),
+                   "bench_step": f"{S} split steps (one CUDA-graph launch of the split-step kernel, "
+                                 f"{S * w.params['dt_split']:.1f} simulated ms)",
+                   "split_steps_timed": split_steps,
                    "path": "plain FP32 (HH Heun x3 + CN/partitioned Thomas x2)",
                    "tuning": tune, "parallelism": f"replicas x{world} (independent fibers)",
-                   "l2": f"state {4 * 4 * total / 1e6:.0f} MB > 129 MB L2, streamed from HBM by every launch"},
+                   "l2": f"state {4 * 4 * total / 1e9:.2f} GB > 129 MB L2, loaded from and stored to HBM by "
+                         f"every launch"},
         "roofline": {
-            "bound": "alu", "achieved": per_gpu_rate / 1e9, "peak": alu_peak / 1e9, "unit": "Gnode-updates/s",
-            "frac": per_gpu_rate / alu_peak, "traffic": traffic,
-            "kernel": "split_step_kernel", "kernel_ms_per_launch": kernel_ms,
-            "algorithmic_bytes_per_launch": BYTES_PER_NODE_UPDATE * total * S,
-            "peak_derivation": f"{n_sm} SMs x {sm_max / 1e6:.0f} MHz / max(FMA {FMA_OPS_PER_NODE_UPDATE:.0f} ops "
-                               f"/ 128 lanes = {fma_clk:.3f} clk, XU {EX2_OPS_PER_NODE_UPDATE:.0f} ex2 / 32 + "
-                               f"{RCP_OPS_PER_NODE_UPDATE:.0f} rcp / 16 = {xu_clk:.3f} clk) per node-update",
-            "hbm_equivalent": {"achieved_gbs": per_gpu_rate * BYTES_PER_NODE_UPDATE / 1e9, "peak_gbs": hbm_peak,
-                               "frac": per_gpu_rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak,
-                               "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved_gbs / hbm_peak,
+            "traffic": None if traffic_per_nu is None else traffic_per_nu * total * S,
+            "traffic_source": (f"{NCU_SUMMARY}: ncu dram__bytes_read.sum + dram__bytes_write.sum per node-update "
+                               f"of the same kernel source and launch shape, scaled to this launch"
+                               if traffic_per_nu is not None else
+                               "null: the kernel changed since the committed ncu capture"),
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "kernel": "split_step_kernel", "kernel_ms_per_launch": launch_ms, "launches_timed": len(per_launch),
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "algorithmic_bytes": f"{BYTES_PER_NODE_UPDATE:.0f} B per node-update (read + write V, m, h, n in FP32) "
+                                 f"x {total} nodes x {S} split steps per launch",
+            "alu": {"bound": "alu", "achieved": per_gpu_rate / 1e9, "peak": alu_peak / 1e9,
+                    "unit": "Gnode-updates/s", "frac": per_gpu_rate / alu_peak,
+                    "peak_derivation": f"{n_sm} SMs x {sm_max / 1e6:.0f} MHz / max(FMA "
+                                       f"{FMA_OPS_PER_NODE_UPDATE:.0f} ops / 128 lanes = {fma_clk:.3f} clk, XU "
+                                       f"{EX2_OPS_PER_NODE_UPDATE:.0f} ex2 / 32 + {RCP_OPS_PER_NODE_UPDATE:.0f} "
+                                       f"rcp / 16 = {xu_clk:.3f} clk) per node-update",
+                    "note": "the state stays on chip for a whole launch, so DRAM traffic is about 1 % of the "
+                            "algorithmic bytes and the special-function and FP32 pipes bind the kernel"},
         },
         "cpu_baseline": cpu,
         "accuracy_vs_oracle": accuracy,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,
-                "includes": "fibers_create + set_stimulus_times from host arrays, step(K), read_vm to host"},
+                "includes": "fibers_create + set_stimulus_times from host arrays, then per benchmark step "
+                            f"step({S}) and read_vm of every node's V into pinned host memory"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "finite": finite,
-        "surrogate": sur,
-        "adaptive": adaptive,
-        "schemes": schemes,
-        "exp_approx": expapx,
-        "full_scale": full,
     }
+    line.update(legs)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -411,41 +456,56 @@ def activation_times(samples, dt):
     return t
 
 
-def surrogate_leg(args, w, tune, stream, dev, total, plain_rate):
-    """Node-updates/s of the surrogate path on the same bundle, and its
-    agreement with the plain FP32 path on 64 firing fibers over 20 ms."""
+def time_steps(fib, stream, dev, steps, chunk):
+    """ms for `steps` split steps enqueued as step(chunk) calls."""
     import torch
-    from paper_2107_07104_gb300 import fibers as F
-    from paper_2107_07104_gb300 import surrogate as S
-    blob = S.load_blob()
-    fib = F.Fibers.from_workload(w, tuning=tune, stream=stream, mode=F.FIB_MODE_SURROGATE)
-    F.fibers_load_surrogate(fib.ctx, blob)
-    fib.step(args.warmup)
-    fib.synchronize()
-    _, fb0 = fib.stats()
+    torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
     e0.record(stream)
-    fib.step(args.steps)
+    for _ in range(steps // chunk):
+        fib.step(chunk)
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    _, fb1 = fib.stats()
-    fib.close()
-    rate = float(total) * args.steps / (ms / 1e3)
-    sub = firing_subset(w)
-    acc = agreement(trajectory(sub), trajectory(sub, mode=F.FIB_MODE_SURROGATE, blob=blob), sub)
-    # per node and split step the step kernel reads and writes u, m, h, n
-    # once (the network pass touches only the listed nodes, about 2 %)
-    sur_bytes = 32.0
+    return e0.elapsed_time(e1)
+
+
+def bundle_7744_leg(args, stream, dev, steps=1000):
+    """The 7744-fiber bundle (88 x 88 x 1481): plain FP32 rate with 100-step graphs."""
+    from paper_2107_07104_gb300 import fibers as F
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
     hbm_peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
-    return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
-            "hbm": {"bytes_per_node_update": sur_bytes, "achieved_gbs": rate * sur_bytes / 1e9, "peak_gbs": hbm_peak,
-                    "frac": rate * sur_bytes / 1e9 / hbm_peak},
-            "network_fraction_of_node_updates": 1.0 - (fb1 - fb0) / (float(total) * args.steps),
-            "accuracy_vs_plain_fp32": acc,
-            "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=100), stream=stream) as fib:
+        fib.step(300)
+        ms = time_steps(fib, stream, dev, steps, 100)
+        finite = bool(np.isfinite(fib.read_vm()).all())
+    rate = float(w.total_nodes) * steps / (ms / 1e3)
+    return {"workload": "bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz",
+            "node_updates_per_s": rate, "ms_per_split_step": ms / steps, "split_steps": steps, "finite": finite,
+            "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak}
+
+
+def ragged_leg(args, stream, dev, steps=2000):
+    """The ragged bundle (20,000 fibers of U{800..2000} nodes, V0 = rest +
+    N(0, 0.5 mV)): the autotuner chooses the launch shape on the bundle's own
+    fibers, then 1000-step CUDA graphs are timed."""
+    from paper_2107_07104_gb300 import fibers as F
+    w = W.ragged_20000(seed=3, t_end_ms=50.0)
+    hbm_peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=1000), stream=stream) as fib:
+        t0 = time.perf_counter()
+        best = fib.autotune(20)
+        t_tune = time.perf_counter() - t0
+        fib.step(1000)
+        ms = time_steps(fib, stream, dev, steps, 1000)
+        finite = bool(np.isfinite(fib.read_vm()).all())
+        tune = fib.tuning
+    rate = float(w.total_nodes) * steps / (ms / 1e3)
+    return {"workload": "ragged 20000 fibers x U{800..2000} nodes, 150 MUs, Poisson 10-40 Hz",
+            "nodes": int(w.total_nodes), "node_updates_per_s": rate, "ms_per_split_step": ms / steps,
+            "split_steps": steps, "graph_steps": 1000, "autotuned": tune, "autotune_s": t_tune,
+            "finite": finite, "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak,
+            "best": best}
 
 
 def firing_subset(w, n=64, seed=9):
@@ -486,71 +546,95 @@ def agreement(a, b, sub):
             "max_abs_mv": float(np.max(np.abs(a - b)))}
 
 
-def exp_approx_leg(args, w, tune, stream, dev, total, plain_rate):
-    """The thesis's exp* approximation (eq:apx-e-function) on the same
-    bundle: node-updates/s, and its agreement with the exact-exponential FP32
-    path on the surrogate's 64-fiber, 20 ms accuracy sample."""
-    import torch
+def surrogate_leg(args, stream, dev, settle_ms=4.0, steps=300):
+    """Surrogate and plain FP32 node-updates/s on the full-scale bundle, both
+    timed from the same state after settle_ms of simulated time (action
+    potentials propagating), and the share of node-updates the network took.
+    Accuracy on held-out fibers (seed 4 of the 7744-fiber bundle, never seen
+    in training) against the plain FP32 path."""
     from paper_2107_07104_gb300 import fibers as F
+    from paper_2107_07104_gb300 import surrogate as S
+    w = rank_workload(0)
+    blob = S.load_blob()
+    settle = int(round(settle_ms / w.params["dt_split"]))
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=100), stream=stream) as fib:
+        fib.step(settle)
+        state = fib.read_state()
+        ms_plain = time_steps(fib, stream, dev, steps, 100)
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=100), stream=stream, mode=F.FIB_MODE_SURROGATE) as fib:
+        F.fibers_load_surrogate(fib.ctx, blob)
+        fib.write_state(state, settle)
+        _, fb0 = fib.stats()
+        ms_sur = time_steps(fib, stream, dev, steps, 100)
+        _, fb1 = fib.stats()
+        finite = bool(np.isfinite(fib.read_vm()).all())
+    rate_p = float(w.total_nodes) * steps / (ms_plain / 1e3)
+    rate_s = float(w.total_nodes) * steps / (ms_sur / 1e3)
+    held = firing_subset(W.bundle_7744(seed=4, t_end_ms=20.0), n=32, seed=4)
+    acc = agreement(trajectory(held), trajectory(held, mode=F.FIB_MODE_SURROGATE, blob=blob), held)
+    return {"workload": WORKLOAD, "timed_from_ms": settle * w.params["dt_split"], "split_steps": steps,
+            "surrogate_node_updates_per_s": rate_s, "plain_fp32_node_updates_per_s": rate_p,
+            "surrogate_vs_plain": rate_s / rate_p, "finite": finite,
+            "network_fraction_of_node_updates": 1.0 - (fb1 - fb0) / (float(w.total_nodes) * steps),
+            "accuracy_vs_plain_fp32_held_out": acc,
+            "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}
+
+
+def exp_approx_leg(args, stream, dev, steps=500):
+    """The thesis's exp* approximation (eq:apx-e-function) on the 7744-fiber
+    bundle: node-updates/s, and its agreement with the exact-exponential FP32
+    path on 64 firing fibers over 20 ms."""
+    from paper_2107_07104_gb300 import fibers as F
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
     wa = w.with_steps(w.n_steps)
     wa.params = dict(w.params, exp_approx=1)
-    with F.Fibers.from_workload(wa, tuning=tune, stream=stream) as fib:
-        fib.step(args.warmup)
-        fib.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        fib.step(args.steps)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-    rate = float(total) * args.steps / (ms / 1e3)
+    with F.Fibers.from_workload(wa, tuning=dict(graph_steps=100), stream=stream) as fib:
+        fib.step(100)
+        ms = time_steps(fib, stream, dev, steps, 100)
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=100), stream=stream) as fib:
+        fib.step(100)
+        ms_p = time_steps(fib, stream, dev, steps, 100)
     sub = firing_subset(w)
-    return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
+    return {"workload": "bundle 7744 fibers x 1481 nodes", "node_updates_per_s": float(w.total_nodes) * steps / (ms / 1e3),
+            "vs_plain_fp32": ms_p / ms,
             "accuracy_vs_plain_fp32": agreement(trajectory(sub), trajectory(sub, exp_approx=1), sub),
             "exp": "exp*(x) = (1 + x/1024)^1024 for every exponential of the rates (FP32 pipe, no ex2)"}
 
 
-def adaptive_leg(args, w, tune, stream, dev, total, plain_rate):
-    """The same bundle with adaptive computation: node-updates/s counted over
-    all nodes (the simulated work), the share of fiber-steps skipped, and the
-    agreement with the plain path at the end of the timed region."""
-    import torch
+def adaptive_leg(args, stream, dev, steps=2000):
+    """The 7744-fiber bundle with adaptive computation: node-updates/s counted
+    over all nodes (the simulated work), the share of fiber-steps skipped,
+    and the agreement with the plain path at the end of the timed region."""
     from paper_2107_07104_gb300 import fibers as F
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
     wa = w.with_steps(w.n_steps)
     wa.params = dict(w.params)
     wa.params["flags"] = F.FIB_FLAG_ADAPTIVE
-    fib = F.Fibers.from_workload(wa, tuning=tune, stream=stream)
-    fib.step(args.warmup)
-    fib.synchronize()
-    s0 = F.fibers_adaptive_stats(fib.ctx)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    fib.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    s1 = F.fibers_adaptive_stats(fib.ctx)
-    va = fib.read_vm().astype(np.float64)
-    fib.close()
-    with F.Fibers.from_workload(w, tuning=tune, stream=stream) as ref:
-        ref.step(args.warmup + args.steps)
+    warm = 200
+    with F.Fibers.from_workload(wa, tuning=dict(graph_steps=100), stream=stream) as fib:
+        fib.step(warm)
+        fib.synchronize()
+        s0 = F.fibers_adaptive_stats(fib.ctx)
+        ms = time_steps(fib, stream, dev, steps, 100)
+        s1 = F.fibers_adaptive_stats(fib.ctx)
+        va = fib.read_vm().astype(np.float64)
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=100), stream=stream) as ref:
+        ref.step(warm)
+        ms_p = time_steps(ref, stream, dev, steps, 100)
         vp = ref.read_vm().astype(np.float64)
-    rate = float(total) * args.steps / (ms / 1e3)
-    return {"value": rate, "unit": UNIT, "ms_per_step": ms / args.steps, "vs_plain_fp32": rate / plain_rate,
-            "skipped_fiber_step_fraction": (s1 - s0) / float(w.n_fibers * args.steps),
+    rate = float(w.total_nodes) * steps / (ms / 1e3)
+    return {"workload": "bundle 7744 fibers x 1481 nodes", "node_updates_per_s": rate, "vs_plain_fp32": ms_p / ms,
+            "timed_from_ms": warm * w.params["dt_split"], "split_steps": steps,
+            "skipped_fiber_step_fraction": (s1 - s0) / float(w.n_fibers * steps),
             "equilibrium_test": "every component of every node changed <= 1e-5 relative over a launch's last "
                                 "split step, and no pulse due in the next launch",
             "max_abs_mv_vs_plain_fp32_at_end": float(np.max(np.abs(va - vp)))}
 
 
-# Scheme variants timed on the same bundle: (name, parameter overrides).  The
-# two thesis configurations compare a first-order scheme at a small step with
-# a second-order one at a large step; their accuracy against a fine reference
-# is measured by the oracle tests, their cost here.
+# Scheme variants timed on the 7744-fiber bundle: (name, parameter
+# overrides).  The two thesis configurations compare a first-order scheme at
+# a small step with a second-order one at a large step; their accuracy
+# against a fine reference is measured by the oracle tests, their cost here.
 SCHEME_LEGS = [
     ("strang 1D-0D-1D, CN, dt 3e-3 (default)", {}),
     ("strang 0D-1D-0D, CN, dt 4e-3, dt_0D 2e-3, dt_1D 4e-3",
@@ -562,11 +646,11 @@ SCHEME_LEGS = [
 ]
 
 
-def schemes_leg(args, w, tune, stream, dev, total, sim_ms=3.0):
-    """Each scheme variant on the bundle over the same simulated interval:
-    node-updates/s per split step and simulated milliseconds per second."""
-    import torch
+def schemes_leg(args, stream, dev, sim_ms=3.0):
+    """Each scheme variant on the 7744-fiber bundle over the same simulated
+    interval: node-updates/s per split step and simulated milliseconds per second."""
     from paper_2107_07104_gb300 import fibers as F
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
     out = {}
     for name, over in SCHEME_LEGS:
         ws = w.with_steps(w.n_steps)
@@ -574,81 +658,31 @@ def schemes_leg(args, w, tune, stream, dev, total, sim_ms=3.0):
         ws.params.update(over)
         dt = ws.params["dt_split"]
         steps = int(round(sim_ms / dt))
-        warm = max(3, steps // 10)
-        with F.Fibers.from_workload(ws, tuning=tune, stream=stream) as fib:
-            fib.step(warm)
-            fib.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            e0.record(stream)
-            fib.step(steps)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
+        steps -= steps % 50
+        with F.Fibers.from_workload(ws, tuning=dict(graph_steps=50), stream=stream) as fib:
+            fib.step(100)
+            ms = time_steps(fib, stream, dev, steps, 50)
             finite = bool(np.all(np.isfinite(fib.read_vm())))
-        out[name] = {"node_updates_per_s": float(total) * steps / (ms / 1e3), "ms_per_step": ms / steps,
+        out[name] = {"node_updates_per_s": float(w.total_nodes) * steps / (ms / 1e3), "ms_per_step": ms / steps,
                      "simulated_ms_per_s": steps * dt / (ms / 1e3), "steps": steps, "finite": finite}
-    return out
-
-
-def full_scale_leg(stream, dev, plain_steps=500, sur_steps=200):
-    """The full-scale bundle (67600 fibers x 1481 nodes = 1.0e8 nodes, 200
-    MUs): plain FP32 and surrogate node-updates/s and HBM fractions on one
-    GPU, each timed after a warm-up with the state resident."""
-    import torch
-    from paper_2107_07104_gb300 import fibers as F
-    from paper_2107_07104_gb300 import surrogate as S
-    w = W.bundle_67600(seed=5, t_end_ms=100.0)
-    hbm_peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
-    out = {"workload": "bundle 67600 fibers x 1481 nodes (260x260), 200 MUs, Poisson 10-30 Hz",
-           "nodes": int(w.total_nodes)}
-    for name, mode, steps in (("plain_fp32", F.FIB_MODE_FP32, plain_steps),
-                              ("surrogate", F.FIB_MODE_SURROGATE, sur_steps)):
-        with F.Fibers.from_workload(w, stream=stream, mode=mode) as fib:
-            if mode == F.FIB_MODE_SURROGATE:
-                F.fibers_load_surrogate(fib.ctx, S.load_blob())
-            fib.step(max(steps // 10, 3))
-            fib.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            with ClockSampler(dev.index if dev.index is not None else 0) as clk:
-                e0.record(stream)
-                fib.step(steps)
-                e1.record(stream)
-                e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            finite = bool(np.all(np.isfinite(fib.read_vm())))
-        rate = float(w.total_nodes) * steps / (ms / 1e3)
-        out[name] = {"node_updates_per_s": rate, "ms_per_step": ms / steps, "steps": steps, "finite": finite,
-                     "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak,
-                     "clocks": clk.summary()}
-    out["surrogate_vs_plain"] = out["surrogate"]["node_updates_per_s"] / out["plain_fp32"]["node_updates_per_s"]
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20, help=f"benchmark steps of {BENCH_SPLIT_STEPS} split steps")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nodes-per-thread", type=int, default=0)
     ap.add_argument("--warps-per-cta", type=int, default=0)
-    ap.add_argument("--steps-per-launch", type=int, default=0)
-    ap.add_argument("--graph-steps", type=int, default=1000)
     ap.add_argument("--reaction-pairs", type=int, default=0, help="1 scalar, 2 packed FP32x2, 0 auto")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="register budget: 2, 3 or 4 CTAs per SM, 0 auto")
-    ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-fibers", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="time the headline workload only")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--no-adaptive", action="store_true")
-    ap.add_argument("--no-schemes", action="store_true")
-    ap.add_argument("--no-exp-approx", action="store_true")
-    ap.add_argument("--no-full-scale", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -506,9 +506,11 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
     }
   }
 
-  // stimulated nodes of this thread and the MU firing cursor
+  // stimulated nodes of this thread and the MU firing cursor; fk caches
+  // fire_k[cur] (INT64_MAX past the end), so a substep's stimulus test reads
+  // global memory only when the cursor moves past an ended pulse
   uint32_t mask = 0;
-  int64_t cur = 0, fend = 0;
+  int64_t cur = 0, fend = 0, fk = INT64_MAX;
   if (fd.mu >= 0 && fd.mu < a.n_mu) {
     const int lo = max(fd.junction - a.hw, 0), hi = min(fd.junction + a.hw, fd.n - 1);
 #pragma unroll
@@ -528,6 +530,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
         else hi_f = mid;
       }
       cur = lo_f;
+      if (cur < fend) fk = a.fire_k[cur];
     }
   }
 
@@ -552,8 +555,11 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
         bool on = false;
         if (mask) {
           const int64_t kk = stp * a.n_sub + k;
-          while (cur < fend && a.fire_k[cur] + a.pulse <= kk) ++cur;
-          on = (cur < fend) && (a.fire_k[cur] <= kk);
+          while (fk != INT64_MAX && fk + a.pulse <= kk) {
+            ++cur;
+            fk = cur < fend ? a.fire_k[cur] : INT64_MAX;
+          }
+          on = fk <= kk;
         }
         if (PACKED) {
           if (on) heun_nodes_packed<K, true, EXPAPX>(u, m, h, n, a.hh, mask);

@@ -107,6 +107,25 @@ def quiet_box(params: dict, du: float = 8.0, dg: float = 0.03):
     return lo, hi
 
 
+def trust_box(params: dict, u_hi: float = 10.0, h_hi: float = 0.35):
+    """Box of raw inputs where the network replaces the plain HH step: the
+    repolarisation tail and the recovery after an action potential (the
+    sodium inactivation gate h at most h_hi, depolarisation at most u_hi mV,
+    no stimulus).  The upstroke (h still near rest while u rises) and every
+    stimulated node stay with the plain step, since errors there move the
+    wavefront; errors behind it decay."""
+    lo = np.array([-100.0, 0.0, 0.0, 0.0, 0.0], np.float32)
+    hi = np.array([u_hi, 1.0, h_hi, 1.0, 0.0], np.float32)
+    return lo, hi
+
+
+def inside_box(X, lo, hi):
+    torch = _torch()
+    l = torch.as_tensor(lo, device=X.device)
+    h = torch.as_tensor(hi, device=X.device)
+    return ((X >= l) & (X <= h)).all(dim=1)
+
+
 def outside_box(X, lo, hi):
     torch = _torch()
     l = torch.as_tensor(lo, device=X.device)
@@ -115,11 +134,13 @@ def outside_box(X, lo, hi):
 
 
 def train(X, Y, epochs: int = 6, batch: int = 8192, lr: float = 2e-3, lr_end: float = 2e-5, seed: int = 0,
-          quantize: bool = True, log: Optional[List[float]] = None, quiet=None,
+          quantize: bool = True, log: Optional[List[float]] = None, quiet=None, trust=None,
           avg_decay: Optional[float] = 0.999) -> np.ndarray:
     """Adam on the normalised data (cosine learning-rate decay); returns the
     blob for fibers_load_surrogate.  Samples inside the quiet box (handled by
-    the plain step at run time) are left out.
+    the plain step at run time) are left out, and so are samples outside the
+    trust box (None: no restriction); the blob's envelope is the box of the
+    samples kept, so the network only sees states like those it learned.
 
     The blob carries the exponential moving average of the weights over the
     steps (decay avg_decay; None: the last step's weights).  On held-out
@@ -130,6 +151,8 @@ def train(X, Y, epochs: int = 6, batch: int = 8192, lr: float = 2e-3, lr_end: fl
     if quiet is None:
         quiet = (np.full(5, 1.0, np.float32), np.full(5, -1.0, np.float32))  # empty box
     keep = outside_box(X, quiet[0], quiet[1])
+    if trust is not None:
+        keep = keep & inside_box(X, trust[0], trust[1])
     X = X[keep].contiguous()
     Y = Y[keep].contiguous()
     xs = F.fibers_feature_stats(X)
@@ -142,6 +165,8 @@ def train(X, Y, epochs: int = 6, batch: int = 8192, lr: float = 2e-3, lr_end: fl
     env_lo = xs[:, 2].astype(np.float32)
     env_hi = xs[:, 3].astype(np.float32)
     env_lo[4], env_hi[4] = 0.0, 1.0
+    if trust is not None:  # the stimulus column is 0 throughout the trust box
+        env_lo[4], env_hi[4] = trust[0][4], trust[1][4]
     Xn = ((X - torch.as_tensor(in_mu, device=dev)) / torch.as_tensor(in_sigma, device=dev)).contiguous()
     Yn = ((Y - torch.as_tensor(out_mu, device=dev)) / torch.as_tensor(out_sigma, device=dev)).contiguous()
     theta = torch.as_tensor(_he_uniform(seed), device=dev).contiguous()
@@ -202,8 +227,10 @@ def training_workloads(seed_single: int = 1, seed_bundle: int = 2, bundle_fibers
 
 
 def build_surrogate(n_samples: int = 16_000_000, epochs: int = 24, seed: int = 0, log: Optional[List[float]] = None,
-                    device: str = "cuda") -> np.ndarray:
-    """Samples from the plain method, trains, and returns the surrogate blob."""
+                    device: str = "cuda", trust: bool = True) -> np.ndarray:
+    """Samples from the plain method, trains, and returns the surrogate blob.
+    With trust, the network is trained on, and later used in, the trust box
+    only (no stimulated samples are drawn then)."""
     torch = _torch()
     ws = training_workloads()
     parts = []
@@ -212,8 +239,9 @@ def build_surrogate(n_samples: int = 16_000_000, epochs: int = 24, seed: int = 0
         cps = np.linspace(50, w.n_steps, 60).astype(int)
         parts.append(sample_states(w, share, cps, seed=seed + 17 * i, device=device))
     states = torch.cat(parts)
-    X, Y = make_dataset(ws[0].params, states, seed=seed + 1)
-    return train(X, Y, epochs=epochs, seed=seed, log=log, quiet=quiet_box(ws[0].params))
+    tb = trust_box(ws[0].params) if trust else None
+    X, Y = make_dataset(ws[0].params, states, seed=seed + 1, stim_fraction=0.0 if trust else 0.15)
+    return train(X, Y, epochs=epochs, seed=seed, log=log, quiet=quiet_box(ws[0].params), trust=tb)
 
 
 def _he_uniform(seed: int) -> np.ndarray:

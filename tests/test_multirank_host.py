@@ -44,7 +44,7 @@ def test_two_ranks_aggregate_without_sharing_fibers():
         assert p.exitcode == 0
     res = sorted(q.get(timeout=10) for _ in range(2))
     (r0, s0, n0, tot0, t0, mu0), (r1, s1, n1, tot1, t1, mu1) = res
-    assert (s0, s1) == (2, 3)              # independent seeded bundles
+    assert (s0, s1) == (5, 6)              # independent seeded bundles
     assert mu0 != mu1
     assert tot0 == tot1 == (n0 + n1) * 10.0  # node-updates summed over ranks
     assert t0 == t1 == 2.0                   # time of the slowest rank

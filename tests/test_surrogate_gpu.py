@@ -9,7 +9,7 @@ from paper_2107_07104_gb300 import fibers as F
 from paper_2107_07104_gb300 import surrogate as S
 from paper_2107_07104_gb300 import workloads as W
 
-from parity import errors, gpu_checkpoints, oracle_checkpoints, select_fibers
+from parity import ACT_TIME_MS, MAX_ABS_MV, REL_L2, errors, gpu_checkpoints, oracle_checkpoints, select_fibers
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -180,10 +180,12 @@ def test_surrogate_on_held_out_bundle(trained_blob):
           f"(missed {int((~np.isnan(to) & np.isnan(ts)).sum())}); fallback node-steps {fb}")
     assert np.isfinite(sur).all()
     fired = ~np.isnan(to)
-    assert both.sum() >= 0.99 * fired.sum()          # activations found where the oracle has them
-    assert (np.isnan(to) & ~np.isnan(ts)).sum() <= 0.01 * fired.sum()  # no spurious excitation
-    assert act <= 0.05                                # activation times within 0.05 ms
-    assert es[1] <= 0.01                              # trajectory relative L2 (max|dV| is reported, not bounded)
+    assert fb < w.n_steps * w.total_nodes             # the network did handle node-steps
+    assert both.sum() == fired.sum()                  # every activation the oracle has
+    assert (np.isnan(to) & ~np.isnan(ts)).sum() == 0  # no spurious excitation
+    assert act <= ACT_TIME_MS                         # activation times within 0.05 ms
+    assert es[0] <= MAX_ABS_MV                        # max|dV| <= 0.5 mV over the trajectory
+    assert es[1] <= REL_L2                            # relative L2 <= 1e-3 over the trajectory
 
 
 def test_surrogate_mode_graphs_match_eager_launches():
