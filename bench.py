@@ -178,10 +178,20 @@ def dram_traffic_per_node_update(tune):
         return None
 
 
-def rank_workload(rank: int):
-    """Each rank simulates its own seeded full-scale bundle: fibers are
-    independent, so ranks share nothing on the data path (weak scaling)."""
-    return W.bundle_67600(seed=5 + rank, t_end_ms=100.0)
+WORKLOADS = {
+    "bundle_67600": ("bundle 67600 fibers x 1481 nodes (260x260), 200 MUs, Poisson 10-30 Hz",
+                     lambda rank: W.bundle_67600(seed=5 + rank, t_end_ms=100.0)),
+    # smaller case for profiler captures (ncu) of the same kernel
+    "bundle_7744": ("bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz",
+                    lambda rank: W.bundle_7744(seed=2 + rank, t_end_ms=20.0)),
+}
+
+
+def rank_workload(rank: int, name: str = "bundle_67600"):
+    """Each rank simulates its own seeded bundle (the full-scale one unless
+    named otherwise): fibers are independent, so ranks share nothing on the
+    data path (weak scaling)."""
+    return WORKLOADS[name][1](rank)
 
 
 def aggregate_over_ranks(node_updates_local: float, seconds_local: float, dist, device=None):
@@ -305,7 +315,8 @@ def run_gpu(args, world, rank, local, dist):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = rank_workload(rank)
+    w = rank_workload(rank, args.workload)
+    workload_name = WORKLOADS[args.workload][0]
     total = w.total_nodes
     S = BENCH_SPLIT_STEPS
     stream = torch.cuda.Stream(device=dev)
@@ -383,7 +394,7 @@ def run_gpu(args, world, rank, local, dist):
     if not args.no_cpu_baseline:
         rate, dt, cores, nodes = oracle_rate(w, args.cpu_fibers, args.cpu_steps)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_fibers} of 67600 fibers x 1481 nodes, {args.cpu_steps} split steps "
+               "sample": f"first {args.cpu_fibers} of {w.n_fibers} fibers x 1481 nodes, {args.cpu_steps} split steps "
                          f"({dt:.1f} s of FP64 oracle on {cores} threads)"}
         accuracy = accuracy_vs_oracle(tune, args.cpu_steps)
     legs = {}
@@ -395,11 +406,12 @@ def run_gpu(args, world, rank, local, dist):
         legs["adaptive"] = adaptive_leg(args, stream, dev)
         legs["schemes"] = schemes_leg(args, stream, dev)
         legs["exp_approx"] = exp_approx_leg(args, stream, dev)
+        legs["emg"] = emg_leg(args, stream, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": (t_max * 1e3) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "fibers": int(w.n_fibers), "nodes": int(total),
+        "config": {"workload": workload_name, "fibers": int(w.n_fibers), "nodes": int(total),
                    "bench_step": f"{S} split steps (one CUDA-graph launch of the split-step kernel, "
                                  f"{S * w.params['dt_split']:.1f} simulated ms)",
                    "split_steps_timed": split_steps,
@@ -580,6 +592,48 @@ def surrogate_leg(args, stream, dev, settle_ms=4.0, steps=300):
             "weights": "paper_2107_07104_gb300/data/hh_surrogate.npy (trained on the GPU by this package)"}
 
 
+def emg_leg(args, stream, dev, settle=1500, reps=5):
+    """The fiber-to-3D coupling on the 7744-fiber bundle (88 x 88 fibers at
+    0.05 cm, 14.8 cm long) with a 30 x 30 x 41 mesh (36,900 nodes): time of
+    the mapping V3D and of the phi_e solve (FP64 conjugate gradients to 1e-8
+    of the right-hand side) 4.5 ms into the run, next to one split step."""
+    import torch
+    from paper_2107_07104_gb300 import fibers as F
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
+    xy = W.fiber_grid_xy(88, 0.05)
+    mp = W.box_mesh(xy, 14.8, 30, 41)
+    mesh = F.make_mesh3d(mp["nx"], mp["ny"], mp["nz"], mp["origin"], mp["spacing"], 8.93, 6.7)
+    with F.Fibers.from_workload(w, tuning=dict(graph_steps=100), stream=stream) as fib:
+        fib.step(settle)
+        t0 = time.perf_counter()
+        emg = F.fibers_emg_create(fib.ctx, xy, 0.0, mesh)
+        t_setup = time.perf_counter() - t0
+        try:
+            n3 = F.fibers_emg_nodes(emg)
+            v3 = torch.empty(n3, dtype=torch.float64, device=dev)
+            phi = torch.empty(n3, dtype=torch.float32, device=dev)
+            F.fibers_emg_phi_e(emg, phi, rtol=1e-8)
+            ms_map, ms_phi, its = [], [], []
+            for _ in range(reps):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                F.fibers_emg_vm3d(emg, v3)
+                ms_map.append(1e3 * (time.perf_counter() - t0))
+                t0 = time.perf_counter()
+                it, res = F.fibers_emg_phi_e(emg, phi, rtol=1e-8)
+                ms_phi.append(1e3 * (time.perf_counter() - t0))
+                its.append(it)
+            finite = bool(torch.isfinite(phi).all().item())
+            peak = float(phi.abs().max().item())
+        finally:
+            F.fibers_emg_destroy(emg)
+    return {"workload": "bundle 7744 fibers x 1481 nodes at 0.05 cm spacing, 3D mesh 30 x 30 x 41",
+            "nodes_3d": int(n3), "fiber_nodes": int(w.total_nodes), "setup_s": t_setup,
+            "vm3d_ms": statistics.median(ms_map), "phi_e_ms_incl_mapping": statistics.median(ms_phi),
+            "cg_iterations": int(statistics.median(its)), "rtol": 1e-8, "max_abs_phi_e_mv": peak,
+            "finite": finite, "timing": "host wall clock around each synchronising call"}
+
+
 def exp_approx_leg(args, stream, dev, steps=500):
     """The thesis's exp* approximation (eq:apx-e-function) on the 7744-fiber
     bundle: node-updates/s, and its agreement with the exact-exponential FP32
@@ -683,6 +737,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="time the headline workload only")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--workload", default="bundle_67600", choices=sorted(WORKLOADS),
+                    help="headline workload (bundle_7744: the smaller case used for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

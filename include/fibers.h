@@ -308,16 +308,19 @@ fib_status fibers_hh_reaction(const fib_params* p, int64_t count, const float* i
  * the gradient of the loss with respect to theta.  With quantize != 0 the
  * forward pass rounds weights and matrix-product inputs to bfloat16 (round to
  * nearest even) as inference does, and the gradient treats that rounding as
- * the identity.
+ * the identity; every matrix product (forward, backward and the weight
+ * gradients) then runs on BF16 tensor cores with FP32 accumulation, with
+ * FP32 left operands split into bf16 high and low parts.  With quantize == 0
+ * the kernels compute in FP32 on the CUDA cores.  Deterministic (no atomics).
  *   theta     17796 floats.      x       batch x 5 normalised inputs.
- *   target    batch x 4.         workspace >= batch x 784 floats (scratch).
+ *   target    batch x 4.         workspace >= batch x 848 floats (scratch).
  *   grad      17796 floats (out). loss   1 float (out, device).
  * Asynchronous.  Errors: FIB_EINVAL, FIB_ECUDA. */
 fib_status fibers_mlp_train_step(const float* theta, int32_t quantize, const float* x, const float* target,
                                  int64_t batch, float* workspace, float* grad, float* loss, void* cuda_stream);
 
 /* Forward pass only: out (batch x 4) for inputs x (batch x 5); workspace >=
- * batch x 512 floats.  Asynchronous. */
+ * batch x 520 floats.  Asynchronous. */
 fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float* x, int64_t batch, float* workspace,
                               float* out, void* cuda_stream);
 
@@ -338,6 +341,74 @@ fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad,
  * X (n x cols, row-major) into out (host, 4 x cols doubles, column by column:
  * mean, std, min, max).  Synchronises cuda_stream.  cols <= 64. */
 fib_status fibers_feature_stats(const float* X, int64_t n, int32_t cols, double* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Coupling to a 3D mesh of the muscle (eq:discretized_fibers): the
+ * transmembrane voltage of the fibers is mapped onto a structured
+ * hexahedral mesh (eq:discretized_fibers_2) and the static first bidomain
+ * equation gives the extracellular potential (eq:discretized_fibers_3,
+ * eq:static_bidomain_rhs):
+ *     K_(sigma_i + sigma_e) phi_e = -K_(sigma_i) V3D
+ * with trilinear finite elements on the mesh, homogeneous Neumann
+ * boundaries (eq:monodomain_bc3), sigma_i = sigma_i a (x) a along the fiber
+ * direction a = z and sigma_e isotropic (eq:multidomain_isotropic_e).
+ * The mapping is the thesis's data mapping between meshes
+ * (sec:data_mapping_between_meshes, eq:mapping_source_target): each fiber
+ * node adds the value of its element's 8 trilinear ansatz functions at its
+ * position as factors to those nodes, and a 3D node's value is the
+ * factor-weighted mean of the fiber nodes that reach it (0 if none does).
+ * The Neumann problem fixes phi_e up to a constant; the library returns the
+ * solution with zero mean over the 3D nodes.
+ * ------------------------------------------------------------------------- */
+
+typedef struct fib_emg fib_emg;
+
+/* Structured 3D mesh: node (i, j, k) at origin + (i, j, k) * spacing, node
+ * index i + nx (j + ny k).  Units cm and mS/cm. */
+typedef struct {
+  int32_t nx, ny, nz;  /* nodes per direction, each >= 2 */
+  int32_t reserved;    /* must be 0 */
+  double origin[3];
+  double spacing[3];   /* > 0 */
+  double sigma_i;      /* intracellular conductivity along the fibers (>= 0), e.g. 8.93 */
+  double sigma_e;      /* extracellular conductivity, isotropic (> 0), e.g. 6.7 */
+} fib_mesh3d;
+
+/* Builds the mapping from the fibers of ctx to the 3D mesh.  Fibers are
+ * straight lines along z: fiber f at (fiber_xy[2f], fiber_xy[2f+1]), its
+ * node i at z = z0 + i h (h of fib_params).  Points outside the mesh are
+ * clamped onto its boundary elements.  ctx must outlive the returned
+ * object, which owns its device memory (mapping in CSR form, about 8 x 8
+ * bytes per fiber node).  Synchronises.  Errors: FIB_EINVAL (sizes,
+ * spacing, conductivities, non-finite positions; message on ctx),
+ * FIB_ENOMEM, FIB_ECUDA, FIB_ENOTSUP (no cooperative launch). */
+fib_status fibers_emg_create(fib_ctx* ctx, const double* fiber_xy, double z0, const fib_mesh3d* mesh,
+                             fib_emg** out);
+
+/* V3D (mV, FP64) of every 3D node for the fibers' current V, into out
+ * (capacity >= nx ny nz; out_is_device selects device or host memory).
+ * Synchronises.  Errors: FIB_EINVAL, FIB_ECUDA (message:
+ * fibers_emg_last_error). */
+fib_status fibers_emg_vm3d(fib_emg* emg, double* out, size_t capacity, int32_t out_is_device);
+
+/* phi_e (mV, written as float) of every 3D node for the fibers' current V:
+ * the mapping, the right-hand side and a Jacobi-preconditioned conjugate
+ * gradient solve in FP64, stopped once the residual is below rtol times
+ * the right-hand side's norm, or after max_iter iterations.  iterations and
+ * rel_residual (nullable) receive what the solve reached.  Synchronises.
+ * Errors: FIB_EINVAL, FIB_ECUDA, FIB_ETIMEOUT (rtol not reached; out holds
+ * the last iterate). */
+fib_status fibers_emg_phi_e(fib_emg* emg, float* out, size_t capacity, int32_t out_is_device, double rtol,
+                            int32_t max_iter, int32_t* iterations, double* rel_residual);
+
+/* Number of 3D nodes (0 for NULL). */
+int64_t fibers_emg_nodes(const fib_emg* emg);
+
+/* Message of the last failing call on emg (never NULL). */
+const char* fibers_emg_last_error(const fib_emg* emg);
+
+/* Frees the mapping and solver memory.  NULL is allowed. */
+void fibers_emg_destroy(fib_emg* emg);
 
 /* Host-only diagnostic (no GPU needed): the coefficient tables of the
  * partitioned tridiagonal solve that fibers_create builds for a fiber of

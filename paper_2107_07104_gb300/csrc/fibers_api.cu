@@ -623,6 +623,8 @@ fib_status fib::ctx_view(fib_ctx* c, fib::CtxView* v) {
   v->vrest = (float)c->p.Vrest;
   v->flag = c->d_flag;
   v->launches = &c->launches;
+  v->n_nodes = c->n_nodes.data();
+  v->h = c->p.h;
   return FIB_OK;
 }
 

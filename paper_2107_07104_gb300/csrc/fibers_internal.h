@@ -159,6 +159,8 @@ struct CtxView {
   float vrest;
   const int32_t* flag;  // device non-finite flag
   int64_t* launches;    // the context's kernel-launch counter
+  const int32_t* n_nodes;  // host: nodes of every fiber (ragged order)
+  double h;             // mesh width along the fibers (cm)
 };
 fib_status ctx_view(fib_ctx* c, CtxView* out);
 fib_status ctx_fail(fib_ctx* c, fib_status s, const char* msg);

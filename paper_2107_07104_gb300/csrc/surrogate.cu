@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "fibers_internal.h"
@@ -406,6 +407,218 @@ __global__ void __launch_bounds__(kSurThreads) sur_net_kernel(const SurArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Training on BF16 tensor cores (quantised mode)
+// ---------------------------------------------------------------------------
+//
+// Every matrix product of a training step is C = A B with mma.sync
+// m16n8k16 BF16 x BF16 -> FP32.  B operands are always exact in bf16 (the
+// quantised weights, or activations and inputs already rounded to bf16 by
+// the forward pass).  A operands that are FP32 (the backward pass's dz and
+// dout) are split into bf16 high and low parts, A = A_hi + A_lo, and both
+// are multiplied, so the product keeps about 16 bits of A's mantissa.  The
+// weight gradients reduce over the batch in fixed chunks of kChunk samples
+// whose partial products are summed in chunk order (deterministic).
+
+constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 16, kGemmThreads = 128, kChunk = 256;
+
+// A(m, k) = A[m * a_m + k * a_k], B(k, n) = B[k * b_k + n * b_n] (FP32 arrays).
+struct GemmOp {
+  const float* A;
+  int64_t a_m, a_k;
+  const float* B;
+  int64_t b_k, b_n;
+  int M, N;
+  int64_t K;
+  int split_a;   // A is FP32: multiply its bf16 high and low parts
+};
+
+enum EpiKind { kEpiSilu, kEpiOut, kEpiDz, kEpiPartial };
+
+struct Epilogue {
+  int kind;
+  const float* bias;     // kEpiSilu, kEpiOut: per-column bias
+  float* z;              // kEpiSilu: pre-activation out (M x N row-major)
+  float* a;              // kEpiSilu: bf16-rounded SiLU out; kEpiDz: dz out
+  const float* zin;      // kEpiDz: pre-activation whose SiLU derivative scales the product
+  float* out;            // kEpiOut: network output; kEpiPartial: partial tiles [chunk][M][N]
+  const float* target;   // kEpiOut
+  float* dout;           // kEpiOut: 2 (out - target) / (B * 4)
+  float scale;
+  int quantize;
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&b);
+}
+
+// One CTA: a kGemmBM x kGemmBN tile of C over k in [k0, k1); 4 warps, each
+// a 32 x 32 quarter as 2 x 4 m16n8 tiles.
+__global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(GemmOp g, Epilogue e, int64_t k_chunk) {
+  __shared__ __align__(16) uint16_t sAh[kGemmBM][kGemmBK + 8];
+  __shared__ __align__(16) uint16_t sAl[kGemmBM][kGemmBK + 8];
+  __shared__ __align__(16) uint16_t sB[kGemmBN][kGemmBK + 8];  // [n][k]: col-major B
+  const int m0 = blockIdx.x * kGemmBM, n0 = blockIdx.y * kGemmBN;
+  const int64_t k0 = (int64_t)blockIdx.z * k_chunk;
+  const int64_t k1 = min(g.K, k0 + k_chunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4] = {};
+  for (int64_t kb = k0; kb < k1; kb += kGemmBK) {
+    for (int i = threadIdx.x; i < kGemmBM * kGemmBK; i += kGemmThreads) {
+      const int mm = i / kGemmBK, kk = i % kGemmBK;
+      const int64_t m = m0 + mm, k = kb + kk;
+      float v = 0.0f;
+      if (m < g.M && k < k1) v = g.A[m * g.a_m + k * g.a_k];
+      const uint16_t hi = bf16_bits(v);
+      sAh[mm][kk] = hi;
+      if (g.split_a) {
+        __nv_bfloat16 hb;
+        *reinterpret_cast<uint16_t*>(&hb) = hi;
+        sAl[mm][kk] = bf16_bits(v - __bfloat162float(hb));
+      }
+    }
+    for (int i = threadIdx.x; i < kGemmBN * kGemmBK; i += kGemmThreads) {
+      const int nn = i / kGemmBK, kk = i % kGemmBK;
+      const int64_t n = n0 + nn, k = kb + kk;
+      float v = 0.0f;
+      if (n < g.N && k < k1) v = g.B[k * g.b_k + n * g.b_n];
+      sB[nn][kk] = bf16_bits(v);  // bf16 values stay exact; FP32 weights round to nearest even
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r = wm + 16 * mt + gq;
+      uint32_t ah[4], al[4];
+      ah[0] = *reinterpret_cast<const uint32_t*>(&sAh[r][2 * tq]);
+      ah[1] = *reinterpret_cast<const uint32_t*>(&sAh[r + 8][2 * tq]);
+      ah[2] = *reinterpret_cast<const uint32_t*>(&sAh[r][2 * tq + 8]);
+      ah[3] = *reinterpret_cast<const uint32_t*>(&sAh[r + 8][2 * tq + 8]);
+      if (g.split_a) {
+        al[0] = *reinterpret_cast<const uint32_t*>(&sAl[r][2 * tq]);
+        al[1] = *reinterpret_cast<const uint32_t*>(&sAl[r + 8][2 * tq]);
+        al[2] = *reinterpret_cast<const uint32_t*>(&sAl[r][2 * tq + 8]);
+        al[3] = *reinterpret_cast<const uint32_t*>(&sAl[r + 8][2 * tq + 8]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = wn + 8 * nt + gq;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sB[c][2 * tq]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sB[c][2 * tq + 8]);
+        mma_bf16(acc[mt][nt], ah, b0, b1);
+        if (g.split_a) mma_bf16(acc[mt][nt], al, b0, b1);
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: element (m, n) of the tile
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + wm + 16 * mt + gq + (q >= 2 ? 8 : 0);
+        const int n = n0 + wn + 8 * nt + 2 * tq + (q & 1);
+        if (m >= g.M || n >= g.N) continue;
+        const float v = acc[mt][nt][q];
+        const int64_t o = (int64_t)m * g.N + n;
+        if (e.kind == kEpiSilu) {
+          const float zz = v + e.bias[n];
+          e.z[o] = zz;
+          e.a[o] = q_bf16(zz / (1.0f + __expf(-zz)), e.quantize);
+        } else if (e.kind == kEpiOut) {
+          const float oo = v + e.bias[n];
+          e.out[o] = oo;
+          if (e.target) e.dout[o] = e.scale * (oo - e.target[o]);
+        } else if (e.kind == kEpiDz) {
+          e.a[o] = v * silu_grad(e.zin[o]);
+        } else {
+          e.out[(int64_t)blockIdx.z * g.M * g.N + o] = v;
+        }
+      }
+}
+
+// W[o] = sum over chunks of partial[c][o] in chunk order; bias gradients as
+// column sums of D (B x cols) over the batch, in fixed order.
+__global__ void reduce_partials_kernel(const float* part, int chunks, int64_t n, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int c = 0; c < chunks; ++c) acc += part[(int64_t)c * n + i];
+    out[i] = acc;
+  }
+}
+
+__global__ void column_sum_kernel(const float* D, int64_t B, int cols, float* out) {
+  __shared__ float part[256];
+  const int c = blockIdx.x;
+  float acc = 0.0f;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) acc += D[b * cols + c];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = part[0];
+}
+
+void gemm(const GemmOp& g, const Epilogue& e, int64_t k_chunk, int chunks, cudaStream_t s) {
+  dim3 grid((g.M + kGemmBM - 1) / kGemmBM, (g.N + kGemmBN - 1) / kGemmBN, chunks);
+  gemm_bf16_kernel<<<grid, kGemmThreads, 0, s>>>(g, e, k_chunk);
+}
+
+// Forward pass of the quantised network on tensor cores: z1, a1, z2, a2,
+// out, and with a target also dout = 2 (out - target) / (B * 4).
+void mma_forward(const float* th, const float* xq, int64_t B, float* z1, float* a1, float* z2, float* a2, float* out,
+                 const float* target, float* dout, cudaStream_t s) {
+  const int Bi = (int)B;
+  Epilogue e{};
+  e.quantize = 1;
+  e.kind = kEpiSilu;
+  GemmOp g1{xq, kIn, 1, th + kOffW1, 1, kIn, Bi, kHid, kIn, 0};  // B(k, j) = W1[j][k]
+  e.bias = th + kOffB1;
+  e.z = z1;
+  e.a = a1;
+  gemm(g1, e, kIn, 1, s);
+  GemmOp g2{a1, kHid, 1, th + kOffW2, 1, kHid, Bi, kHid, kHid, 0};
+  e.bias = th + kOffB2;
+  e.z = z2;
+  e.a = a2;
+  gemm(g2, e, kHid, 1, s);
+  GemmOp g3{a2, kHid, 1, th + kOffW3, 1, kHid, Bi, kOut, kHid, 0};
+  Epilogue eo{};
+  eo.kind = kEpiOut;
+  eo.bias = th + kOffB3;
+  eo.out = out;
+  eo.target = target;
+  eo.dout = dout;
+  eo.scale = 2.0f / (float)(B * kOut);
+  gemm(g3, eo, kHid, 1, s);
+}
+
+// Weight gradient W(M x N) = sum_b A(m, b) B(b, n) over the batch in chunks
+// of about kChunk samples (as many as `part_floats` of partials hold), then
+// the chunk partials summed in order; a single chunk writes W directly.
+void mma_wgrad(GemmOp g, float* part, int64_t part_floats, float* gW, cudaStream_t s) {
+  const int64_t n = (int64_t)g.M * g.N;
+  int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((g.K + kChunk - 1) / kChunk, part_floats / n));
+  int64_t k_chunk = (g.K + chunks - 1) / chunks;
+  k_chunk = (k_chunk + kGemmBK - 1) / kGemmBK * kGemmBK;
+  chunks = (g.K + k_chunk - 1) / k_chunk;
+  Epilogue e{};
+  e.kind = kEpiPartial;
+  e.out = chunks == 1 ? gW : part;
+  gemm(g, e, k_chunk, (int)chunks, s);
+  if (chunks > 1) reduce_partials_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(part, (int)chunks, n, gW);
+}
+
+__global__ void quantize_kernel(const float* x, int64_t n, float* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = q_bf16(x[i], 1);
+}
+
 }  // namespace
 
 size_t sur_smem_bytes() {
@@ -433,6 +646,33 @@ int launch_mlp_train_step(const float* th, int quantize, const float* x, const f
   float* dout = out + B * kOut;
   float* dz1 = dout + B * kOut;
   float* dz2 = dz1 + B * kHid;
+  if (quantize) {
+    // BF16 tensor cores: forward, backward and the weight gradients
+    float* xq = dz2 + B * kHid;                 // B x 5
+    float* part = xq + B * kIn;                 // chunk partials of the weight gradients
+    quantize_kernel<<<(int)((B * kIn + 255) / 256), 256, 0, s>>>(x, B * kIn, xq);
+    mma_forward(th, xq, B, z1, a1, z2, a2, out, target, dout, s);
+    mse_kernel<<<1, 256, 0, s>>>(out, target, B * kOut, loss);
+    const int Bi = (int)B;
+    Epilogue e{};
+    e.kind = kEpiDz;
+    GemmOp d2{dout, kOut, 1, th + kOffW3, kHid, 1, Bi, kHid, kOut, 1};  // da2 = dout W3
+    e.a = dz2;
+    e.zin = z2;
+    gemm(d2, e, kOut, 1, s);
+    GemmOp d1{dz2, kHid, 1, th + kOffW2, kHid, 1, Bi, kHid, kHid, 1};   // da1 = dz2 W2
+    e.a = dz1;
+    e.zin = z1;
+    gemm(d1, e, kHid, 1, s);
+    const int64_t part_floats = B * (kWorkPerSample - 6 * kHid - 2 * kOut - kIn);
+    mma_wgrad(GemmOp{dout, 1, kOut, a2, kHid, 1, kOut, kHid, B, 1}, part, part_floats, grad + kOffW3, s);
+    mma_wgrad(GemmOp{dz2, 1, kHid, a1, kHid, 1, kHid, kHid, B, 1}, part, part_floats, grad + kOffW2, s);
+    mma_wgrad(GemmOp{dz1, 1, kHid, xq, kIn, 1, kHid, kIn, B, 1}, part, part_floats, grad + kOffW1, s);
+    column_sum_kernel<<<kOut, 256, 0, s>>>(dout, B, kOut, grad + kOffB3);
+    column_sum_kernel<<<kHid, 256, 0, s>>>(dz2, B, kHid, grad + kOffB2);
+    column_sum_kernel<<<kHid, 256, 0, s>>>(dz1, B, kHid, grad + kOffB1);
+    return (int)cudaGetLastError();
+  }
   const int grid = (int)(B < 152 * 8 ? B : 152 * 8);
   mlp_fwd_kernel<<<grid, kHid, kFwdSmem, s>>>(th, quantize, x, B, z1, a1, z2, a2, out);
   mse_kernel<<<1, 256, 0, s>>>(out, target, B * kOut, loss);
@@ -452,6 +692,12 @@ int launch_mlp_forward(const float* th, int quantize, const float* x, int64_t B,
   float* a1 = z1 + B * kHid;
   float* z2 = a1 + B * kHid;
   float* a2 = z2 + B * kHid;
+  if (quantize) {
+    float* xq = a2 + B * kHid;
+    quantize_kernel<<<(int)((B * kIn + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, B * kIn, xq);
+    mma_forward(th, xq, B, z1, a1, z2, a2, out, nullptr, nullptr, (cudaStream_t)stream);
+    return (int)cudaGetLastError();
+  }
   const int grid = (int)(B < 152 * 8 ? B : 152 * 8);
   mlp_fwd_kernel<<<grid, kHid, kFwdSmem, (cudaStream_t)stream>>>(th, quantize, x, B, z1, a1, z2, a2, out);
   return (int)cudaGetLastError();

@@ -16,8 +16,10 @@ constexpr int64_t kOffB2 = kOffW2 + kHid * kHid;
 constexpr int64_t kOffW3 = kOffB2 + kHid;
 constexpr int64_t kOffB3 = kOffW3 + kOut * kHid;
 constexpr int64_t kNumParams = kOffB3 + kOut;
-// Floats of training workspace per sample: z1, a1, z2, a2, out, dout, dz1, dz2.
-constexpr int64_t kWorkPerSample = 6 * kHid + 2 * kOut;
+// Floats of training workspace per sample: z1, a1, z2, a2, out, dout, dz1,
+// dz2, the bf16-rounded inputs (5) and the weight gradients' partial sums
+// over chunks of 256 samples (128 x 128 / 256 = 64), rounded up to 848.
+constexpr int64_t kWorkPerSample = 848;
 // bf16 row strides of the inference weight images (padded for conflict-free
 // shared-memory fragment loads): W1 rows hold [x_hi (5) | x_lo (5) | 0].
 constexpr int kW1Stride = 24;

@@ -37,10 +37,11 @@ EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_s
             "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
             "fibers_kernel_launches", "fibers_last_error", "fibers_destroy", "fibers_load_surrogate",
             "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward", "fibers_adam_step",
-            "fibers_feature_stats", "fibers_adaptive_stats", "fibers_solver_tables")
+            "fibers_feature_stats", "fibers_adaptive_stats", "fibers_solver_tables", "fibers_emg_create",
+            "fibers_emg_vm3d", "fibers_emg_phi_e", "fibers_emg_nodes", "fibers_emg_last_error", "fibers_emg_destroy")
 SUR_N_PARAMS = 17796
 SUR_BLOB_FLOATS = 3 + 5 + 5 + 4 + 4 + 5 + 5 + 5 + 5 + SUR_N_PARAMS
-SUR_WORK_PER_SAMPLE = 6 * 128 + 2 * 4
+SUR_WORK_PER_SAMPLE = 848
 
 
 class FibersError(RuntimeError):
@@ -56,6 +57,12 @@ class FibParams(ctypes.Structure):
                  "dt_split", "dt_0d", "dt_1d", "stim_amplitude", "stim_duration")] + \
                [("stim_half_width", ctypes.c_int32), ("mode", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("splitting", ctypes.c_int32), ("diffusion", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class FibMesh3D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double * 3), ("sigma_i", ctypes.c_double),
+                ("sigma_e", ctypes.c_double)]
 
 
 class FibTuning(ctypes.Structure):
@@ -118,6 +125,15 @@ def load(build_if_missing: bool = True):
         L.fibers_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, f32, vp]
         L.fibers_feature_stats.argtypes = [vp, i64, i32, f64p, vp]
         L.fibers_solver_tables.argtypes = [i32, ctypes.c_double, i32, i32, P(i32), P(i32), f64p, f64p]
+        L.fibers_emg_create.argtypes = [vp, f64p, ctypes.c_double, P(FibMesh3D), P(vp)]
+        L.fibers_emg_vm3d.argtypes = [vp, vp, sz, i32]
+        L.fibers_emg_phi_e.argtypes = [vp, vp, sz, i32, ctypes.c_double, i32, P(i32), f64p]
+        L.fibers_emg_nodes.argtypes = [vp]
+        L.fibers_emg_nodes.restype = i64
+        L.fibers_emg_last_error.argtypes = [vp]
+        L.fibers_emg_last_error.restype = ctypes.c_char_p
+        L.fibers_emg_destroy.argtypes = [vp]
+        L.fibers_emg_destroy.restype = None
         for name in ("fibers_load_surrogate", "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward",
                      "fibers_adam_step", "fibers_feature_stats", "fibers_solver_tables"):
             getattr(L, name).restype = ctypes.c_int
@@ -337,6 +353,62 @@ def fibers_solver_tables(K: int, r: float, n_nodes: int, fp64_solve: bool = Fals
                                   _ptr(rows, ctypes.c_double), _ptr(recs, ctypes.c_double)), None)
     return dict(levels=lv.value, threads=tw.value, rows=rows.reshape(2, K, 5),
                 recs=recs.reshape(tw.value, 7 + 3 * lv.value))
+
+
+def _check_emg(status: int, emg) -> None:
+    if status != FIB_OK:
+        msg = load().fibers_emg_last_error(emg)
+        raise FibersError(status, msg.decode() if msg else "")
+
+
+def make_mesh3d(nx, ny, nz, origin, spacing, sigma_i=8.93, sigma_e=6.7) -> FibMesh3D:
+    m = FibMesh3D()
+    m.nx, m.ny, m.nz, m.reserved = int(nx), int(ny), int(nz), 0
+    for d in range(3):
+        m.origin[d] = float(origin[d])
+        m.spacing[d] = float(spacing[d])
+    m.sigma_i, m.sigma_e = float(sigma_i), float(sigma_e)
+    return m
+
+
+def fibers_emg_create(ctx, fiber_xy, z0: float, mesh: FibMesh3D):
+    xy = _arr(fiber_xy, np.float64).reshape(-1)
+    out = ctypes.c_void_p()
+    _check(load().fibers_emg_create(ctx, _ptr(xy, ctypes.c_double), float(z0), ctypes.byref(mesh),
+                                    ctypes.byref(out)), ctx)
+    return out
+
+
+def fibers_emg_vm3d(emg, out) -> None:
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise TypeError("expected a contiguous float64 array")
+        ptr, n, dev = out.ctypes.data, out.size, 0
+    else:
+        import torch
+        if out.dtype != torch.float64 or not out.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
+    _check_emg(load().fibers_emg_vm3d(emg, ptr, n, dev), emg)
+
+
+def fibers_emg_phi_e(emg, out, rtol: float = 1e-10, max_iter: int = 5000):
+    """Solves for phi_e into out; returns (iterations, relative residual)."""
+    ptr, n, dev = _buffer(out)
+    it = ctypes.c_int32()
+    res = ctypes.c_double()
+    _check_emg(load().fibers_emg_phi_e(emg, ptr, n, dev, float(rtol), int(max_iter), ctypes.byref(it),
+                                       ctypes.byref(res)), emg)
+    return int(it.value), float(res.value)
+
+
+def fibers_emg_nodes(emg) -> int:
+    return int(load().fibers_emg_nodes(emg))
+
+
+def fibers_emg_destroy(emg) -> None:
+    if emg:
+        load().fibers_emg_destroy(emg)
 
 
 def fibers_kernel_launches(ctx) -> int:

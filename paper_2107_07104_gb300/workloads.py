@@ -258,3 +258,22 @@ def stratified_by_length(n_nodes: np.ndarray, count: int, seed: int) -> np.ndarr
 def random_fibers(n_fibers: int, count: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n_fibers, size=min(count, n_fibers), replace=False)).astype(np.int64)
+
+
+def fiber_grid_xy(n_side: int, spacing_cm: float = 0.05) -> np.ndarray:
+    """(n_side^2, 2) positions of straight parallel fibers on a square grid in
+    the cross-section, fiber f at ((f % n_side) s, (f // n_side) s): the
+    synthetic stand-in for a muscle cross-section (the 88 x 88 bundle spans
+    4.35 cm, about a biceps belly)."""
+    f = np.arange(n_side * n_side)
+    return np.stack([(f % n_side) * spacing_cm, (f // n_side) * spacing_cm], axis=1).astype(np.float64)
+
+
+def box_mesh(fiber_xy: np.ndarray, length_cm: float, n_xy: int, n_z: int) -> dict:
+    """A structured 3D mesh spanning the fibers' bounding box and their
+    length: n_xy x n_xy x n_z nodes (parameters for fibers_emg_create)."""
+    lo = fiber_xy.min(axis=0)
+    hi = fiber_xy.max(axis=0)
+    return dict(nx=n_xy, ny=n_xy, nz=n_z, origin=(float(lo[0]), float(lo[1]), 0.0),
+                spacing=(float(hi[0] - lo[0]) / (n_xy - 1), float(hi[1] - lo[1]) / (n_xy - 1),
+                         float(length_cm) / (n_z - 1)))

@@ -94,3 +94,64 @@ def edge_workload(n_steps, seed=11, amp=None):
     if amp is not None:
         w.params["stim_amplitude"] = amp
     return w
+
+
+def subset_indices(w, fibers) -> np.ndarray:
+    off = w.offsets()
+    return np.concatenate([np.arange(off[f], off[f + 1]) for f in fibers]).astype(np.int64)
+
+
+def gpu_subset_trajectory(w, fibers, every: int, tuning: Optional[dict] = None, autotune: bool = False):
+    """V (float64) of the nodes of `fibers` after every `every` split steps
+    over the workload's horizon, through the CUDA path at full size; read_vm
+    writes into device memory and the subset is picked out there.  Returns
+    (samples, the launch shape that ran)."""
+    import torch
+    idx = torch.as_tensor(subset_indices(w, fibers), device="cuda")
+    n_s = w.n_steps // every
+    out = torch.empty((n_s, idx.numel()), dtype=torch.float32, device="cuda")
+    buf = torch.empty(w.total_nodes, dtype=torch.float32, device="cuda")
+    with F.Fibers.from_workload(w, tuning=tuning) as fib:
+        if autotune:
+            fib.autotune(20)
+        for i in range(n_s):
+            fib.step(every)
+            F.read_vm(fib.ctx, buf)
+            out[i] = buf.index_select(0, idx)
+        shape = fib.tuning
+    return out.cpu().numpy().astype(np.float64), shape
+
+
+def oracle_subset_trajectory(w, fibers, every: int) -> np.ndarray:
+    """Oracle V of `fibers` (run alone: fibers are independent) after every
+    `every` split steps."""
+    sub = w.subset(fibers)
+    state = oracle.init_state(sub.params, sub.total_nodes, sub.vm0)
+    n_s = w.n_steps // every
+    return oracle.run(sub.params, sub.n_nodes, sub.mu_of_fiber, sub.junction, sub.mu_offsets, sub.fire_times,
+                      state, 0, n_s * every, every)
+
+
+def dense_parity(w, fibers, every: int, tuning: Optional[dict] = None, autotune: bool = False):
+    """GPU and oracle trajectories of the subset (oracle in a host thread
+    while the GPU runs), their errors and the activation-time difference."""
+    import threading
+    res = {}
+    th = threading.Thread(target=lambda: res.setdefault("o", oracle_subset_trajectory(w, fibers, every)))
+    th.start()
+    g, shape = gpu_subset_trajectory(w, fibers, every, tuning, autotune)
+    th.join()
+    o = res["o"]
+    mx, rel = errors(g, o)
+    dt = every * w.params["dt_split"]
+    tg, to = activation_times(g, dt), activation_times(o, dt)
+    # a node activated on one side only must be one whose activation falls
+    # within the tolerance of the last sample (the other side crosses after it)
+    one_side = np.isnan(tg) != np.isnan(to)
+    t_one = np.where(np.isnan(tg), to, tg)[one_side]
+    t_last = g.shape[0] * dt
+    same_set = bool(np.all(t_one >= t_last - ACT_TIME_MS - dt))
+    fired = ~np.isnan(to) & ~np.isnan(tg)
+    act = float(np.max(np.abs(tg[fired] - to[fired]))) if fired.any() else 0.0
+    return dict(max_abs=mx, rel_l2=rel, act=act, same_activated=same_set, activated=int(fired.sum()),
+                samples=int(g.shape[0]), shape=shape)

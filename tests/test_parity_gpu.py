@@ -10,8 +10,8 @@ import oracle
 from paper_2107_07104_gb300 import fibers as F
 from paper_2107_07104_gb300 import workloads as W
 
-from parity import (ACT_TIME_MS, MAX_ABS_MV, REL_L2, activation_times, edge_workload, errors, gpu_checkpoints,
-                    oracle_checkpoints, select_fibers)
+from parity import (ACT_TIME_MS, MAX_ABS_MV, REL_L2, activation_times, dense_parity, edge_workload, errors,
+                    gpu_checkpoints, oracle_checkpoints, select_fibers)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,48 +64,58 @@ def test_ragged_edge_lengths_every_tuning(K, Wc):
     assert o.max() > 0
 
 
-def test_bundle_7744_sampled_fibers_full_size():
-    """7744 x 1481, 100 MUs, 20 ms (6667 steps) in the benchmark's launch
-    configuration; 12 seeded fibers compared with the oracle at checkpoints."""
-    w = W.bundle_7744(seed=2, t_end_ms=20.0)
-    cps = [2000, 4000, 6000, w.n_steps]
-    g = gpu_checkpoints(w, cps)
-    fibers = W.random_fibers(w.n_fibers, 12, seed=102)
-    # include fibers of motor units that fire within the interval
+def _firing_and_random(w, n_firing, n_random, seed):
     firing = [f for f in range(w.n_fibers)
               if w.mu_offsets[w.mu_of_fiber[f] + 1] > w.mu_offsets[w.mu_of_fiber[f]]]
-    fibers = np.unique(np.concatenate([fibers, np.random.default_rng(7).choice(firing, 6, replace=False)]))
-    o = oracle_checkpoints(w, cps, fibers)
-    e = errors(select_fibers(w, g, fibers), o)
-    _report("bundle 7744x1481 sampled", e)
-    assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
-    assert np.isfinite(g).all()
+    rng = np.random.default_rng(seed)
+    pick = np.concatenate([rng.choice(firing, min(n_firing, len(firing)), replace=False),
+                           W.random_fibers(w.n_fibers, n_random, seed=seed + 1)])
+    return np.unique(pick)
 
 
-def test_ragged_20000_sampled_fibers_full_size():
-    """20000 fibers of 800-2000 nodes, 150 MUs, 50 ms (16667 steps), CUDA
-    graphs of 1000 steps; 12 length-stratified fibers against the oracle."""
+def _check_dense(name, r):
+    print(f"[parity] {name}: every 10 split steps x {r['samples']} samples, max|dV| = {r['max_abs']:.3e} mV, "
+          f"rel L2 = {r['rel_l2']:.3e}, activation-time max error {r['act']:.3e} ms over {r['activated']} nodes, "
+          f"shape {r['shape']}")
+    assert r["max_abs"] <= MAX_ABS_MV and r["rel_l2"] <= REL_L2
+    assert r["same_activated"] and r["activated"] > 0
+    assert r["act"] <= ACT_TIME_MS
+
+
+def test_bundle_7744_dense_trajectory():
+    """7744 x 1481, 100 MUs, 20 ms (6667 steps), in the benchmark's launch
+    shape: 40 seeded fibers (32 of firing motor units) compared with the
+    oracle every 10 split steps over the whole run, activation times included."""
+    w = W.bundle_7744(seed=2, t_end_ms=20.0)
+    fibers = _firing_and_random(w, 32, 8, seed=102)
+    _check_dense("bundle 7744x1481", dense_parity(w, fibers, 10, tuning=dict(graph_steps=100)))
+
+
+def test_ragged_20000_dense_trajectory_autotuned():
+    """20000 fibers of 800-2000 nodes, 150 MUs, noisy start, 50 ms (16667
+    steps), in the launch shape the autotuner picks for the bundle: 24
+    length-stratified fibers every 10 split steps."""
     w = W.ragged_20000(seed=3, t_end_ms=50.0)
-    cps = [5000, 10000, w.n_steps]
-    g = gpu_checkpoints(w, cps)
-    fibers = W.stratified_by_length(w.n_nodes, 12, seed=103)
-    o = oracle_checkpoints(w, cps, fibers)
-    e = errors(select_fibers(w, g, fibers), o)
-    _report("ragged 20000 sampled", e)
-    assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
+    fibers = W.stratified_by_length(w.n_nodes, 24, seed=103)
+    _check_dense("ragged 20000", dense_parity(w, fibers, 10, autotune=True))
 
 
-@pytest.mark.slow
-def test_bundle_67600_sampled_fibers_full_size():
-    """67600 x 1481 (1.0e8 nodes), 200 MUs, 100 ms (33334 steps)."""
+def test_ragged_20000_graphs_of_1000_steps_autotuned():
+    """The same bundle in 1000-step CUDA graphs with the autotuned shape,
+    compared at every graph boundary (16 of them)."""
+    w = W.ragged_20000(seed=3, t_end_ms=50.0)
+    fibers = W.stratified_by_length(w.n_nodes, 24, seed=103)
+    r = dense_parity(w, fibers, 1000, tuning=dict(graph_steps=1000), autotune=True)
+    print(f"[parity] ragged 20000, graphs of 1000 steps: max|dV| = {r['max_abs']:.3e} mV, rel L2 = {r['rel_l2']:.3e}")
+    assert r["max_abs"] <= MAX_ABS_MV and r["rel_l2"] <= REL_L2
+
+
+def test_bundle_67600_dense_trajectory():
+    """67600 x 1481 (1.0e8 nodes), 200 MUs, 100 ms (33334 steps): 24 seeded
+    fibers (16 of firing motor units) every 10 split steps."""
     w = W.bundle_67600(seed=5, t_end_ms=100.0)
-    cps = [12000, 24000, w.n_steps]
-    g = gpu_checkpoints(w, cps)
-    fibers = W.random_fibers(w.n_fibers, 8, seed=105)
-    o = oracle_checkpoints(w, cps, fibers)
-    e = errors(select_fibers(w, g, fibers), o)
-    _report("bundle 67600 sampled", e)
-    assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
+    fibers = _firing_and_random(w, 16, 8, seed=105)
+    _check_dense("bundle 67600x1481", dense_parity(w, fibers, 10))
 
 
 def test_subthreshold_stimulus_parity():
