@@ -210,17 +210,21 @@ fib_status read_vm(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_dev
 fib_status read_vm_static(fib_ctx* ctx, float* host_out, size_t capacity);
 
 /* Copies the full state into out (capacity >= 4 sum(n_nodes)): four blocks
- * of sum(n_nodes) floats in ragged order, u | m | h | n, where u = V - Vrest
- * is the depolarisation in mV (the form the library integrates; V itself is
- * u + Vrest) and m, h, n are the HH gates.  The copy is bit-exact, so it can
- * serve as a checkpoint.  Synchronises.  Same errors as read_vm.
+ * of sum(n_nodes) floats in ragged order, u | dm | dh | dn, in the form the
+ * library integrates: u = V - Vrest is the depolarisation in mV, and each HH
+ * gate is held as its deviation from the resting value, dm = m - m0 and so
+ * on, with (Vrest, m0, h0, n0) given by fibers_rest_state.  (In FP32 an
+ * absolute gate near rest stops relaxing once a Heun increment falls below
+ * half a unit in its last place; the deviation keeps full relative
+ * precision, as u does for V.)  The copy is bit-exact, so it can serve as a
+ * checkpoint.  Synchronises.  Same errors as read_vm.
  * Thesis: the state vector y = (V, m, h, n) of every model instance
  * (eq:subcellular); the thesis copies back only the subset needed for
  * output (section "Code Generation for GPUs") and has no checkpoint call. */
 fib_status fibers_read_state(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
 
-/* Replaces the full state with in (layout of fibers_read_state: u | m | h |
- * n) and sets the index of the next split step to step_index (>= 0).  Used
+/* Replaces the full state with in (layout of fibers_read_state: u | dm | dh
+ * | dn) and sets the index of the next split step to step_index (>= 0).  Used
  * for checkpoint / resume: k steps, read_state, write_state, n - k steps
  * gives bit-for-bit the same state as n steps.  Clears a pending non-finite
  * flag, and in surrogate mode empties the network-node lists.  The thesis
@@ -428,6 +432,14 @@ void fibers_emg_destroy(fib_emg* emg);
  * or not finite; a zero pivot). */
 fib_status fibers_solver_tables(int32_t K, double r, int32_t n_nodes, int32_t fp64_solve, int32_t* levels,
                                 int32_t* threads, double* rows, double* recs);
+
+/* The resting state the library uses for parameters p (host only, no
+ * GPU): out[0] = Vrest, out[1..3] = the steady-state gates m0, h0, n0 of
+ * the HH rates at Vrest (sec:subcelullar_model; exp* rates with
+ * FIB_FLAG_EXP_APPROX), as floats.  fibers_read_state's gate blocks are
+ * deviations from these values.  Errors: FIB_EINVAL (invalid parameters or
+ * out NULL). */
+fib_status fibers_rest_state(const fib_params* p, float* out);
 
 /* Number of launches of this library's kernels enqueued so far by ctx (a
  * diagnostic of this library, no thesis counterpart; 0 for ctx == NULL). */

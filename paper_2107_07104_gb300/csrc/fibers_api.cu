@@ -416,6 +416,9 @@ StepArgs make_args(fib_ctx* c) {
   a.step_base = c->d_step;
   a.flag = c->d_flag;
   a.hh = hh_const(c->p, c->EL);
+  a.hh.m0 = (float)c->m0;  // the state arrays hold gate deviations from rest
+  a.hh.h0 = (float)c->h0;
+  a.hh.n0 = (float)c->n0;
   a.r = c->r;
   a.n_sub = (int32_t)c->n_sub;
   a.n_cn = (int32_t)c->n_cn;
@@ -531,8 +534,7 @@ fib_status gather_state(fib_ctx* c, float* dst) {
 fib_status scatter_state(fib_ctx* c, const float* src) {
   if (c->d_quiet) CU(c, cudaMemsetAsync(c->d_quiet, 0, std::max<size_t>(c->n_fibers, 1), c->stream));
   fib_status st = check_launch(c, launch_fill_layout(c->d_fibers, c->n_fibers, st_u(c), st_m(c), st_h(c), st_n(c),
-                                                     nullptr, (float)c->p.Vrest, (float)c->m0, (float)c->h0,
-                                                     (float)c->n0, c->stream),
+                                                     nullptr, (float)c->p.Vrest, 0.0f, 0.0f, 0.0f, c->stream),
                                "fill");
   if (st != FIB_OK) return st;
   ++c->launches;
@@ -590,6 +592,10 @@ fib_status surrogate_steps(fib_ctx* c, cudaStream_t stream, int64_t n) {
     s.out_mu[k] = c->out_mu[k];
     s.out_sigma[k] = c->out_sigma[k];
   }
+  s.rest[0] = 0.0f;
+  s.rest[1] = (float)c->m0;
+  s.rest[2] = (float)c->h0;
+  s.rest[3] = (float)c->n0;
   const int32_t n_cn = (int32_t)c->n_cn;
   fib_status st = FIB_OK;
   for (int64_t i = 0; i < n; ++i) {
@@ -720,9 +726,9 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
       st = fail(cx, FIB_ECUDA, "vm0 upload: %s", cudaGetErrorString(e));
   }
   if (st == FIB_OK) {
+    // gates start at rest: zero deviation in the state arrays
     st = check_launch(cx, launch_fill_layout(cx->d_fibers, cx->n_fibers, st_u(cx), st_m(cx), st_h(cx), st_n(cx), d_vm0,
-                                             (float)p->Vrest, (float)cx->m0, (float)cx->h0, (float)cx->n0,
-                                             cx->stream),
+                                             (float)p->Vrest, 0.0f, 0.0f, 0.0f, cx->stream),
                       "fill");
     ++cx->launches;
   }
@@ -1033,6 +1039,19 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
 }
 
 int64_t fibers_kernel_launches(const fib_ctx* c) { return c ? c->launches : 0; }
+
+fib_status fibers_rest_state(const fib_params* p, float* out) {
+  fib_status st = validate(p);
+  if (st != FIB_OK) return st;
+  if (!out) return fail(nullptr, FIB_EINVAL, "out is NULL");
+  double m0, h0, n0;
+  rest_gates(0.0, &m0, &h0, &n0, (p->flags & FIB_FLAG_EXP_APPROX) != 0);
+  out[0] = (float)p->Vrest;
+  out[1] = (float)m0;
+  out[2] = (float)h0;
+  out[3] = (float)n0;
+  return FIB_OK;
+}
 
 fib_status fibers_solver_tables(int32_t K, double r, int32_t n_nodes, int32_t fp64_solve, int32_t* levels,
                                 int32_t* threads, double* rows, double* recs) {

@@ -49,6 +49,11 @@ struct HHConst {  // Hodgkin-Huxley constants in the depolarisation u = V - Vres
   float stim;         // stimulus amplitude / Cm
   float dt0;          // Heun substep width
   float gNa_uNa, gK_uK, gL_uL;  // products of the above, rounded once from FP64
+  // The state arrays hold each gate as its deviation from the resting value
+  // (g - g0), as u holds V - Vrest: near rest FP32 then resolves the slow
+  // gates' relaxation, which in absolute form stalls once an increment falls
+  // below half an ulp of g.  Zero for callers whose gates are absolute.
+  float m0, h0, n0;
 };
 
 
@@ -138,7 +143,8 @@ int launch_gather(const FiberDesc* fibers, int32_t n_fibers, const float* src, f
 int launch_scatter(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,
                    float add, void* stream);
 // Fills every slot: u = vm0 - vrest on real nodes (0 without vm0 and on
-// padding), gates = (m0, h0, n0) everywhere.
+// padding), gates = (m0, h0, n0) everywhere (the contexts pass zeros: their
+// state holds gate deviations from rest).
 int launch_fill_layout(const FiberDesc* fibers, int32_t n_fibers, float* u, float* m, float* h,
                        float* n, const float* vm0_compact, float vrest, float m0, float h0, float n0,
                        void* stream);

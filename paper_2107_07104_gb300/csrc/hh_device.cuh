@@ -138,7 +138,9 @@ __device__ __forceinline__ Deriv hh_rhs(float u, float m, float h, float n, floa
 
 // One Heun substep (eq:heun) of every node a thread holds.  STIM: the
 // thread owns at least one junction node and the pulse is on; `mask` has
-// bit j set for stimulated nodes.
+// bit j set for stimulated nodes.  The gate arrays hold g - (c.m0, c.h0,
+// c.n0): the right-hand sides and the predictor use absolute gates, the
+// corrector accumulates into the deviations.
 template <int K, bool STIM, bool EXPAPX = false>
 __device__ __forceinline__ void heun_nodes(float (&u)[K], float (&m)[K], float (&h)[K], float (&n)[K],
                                            const HHConst& c, uint32_t mask) {
@@ -146,11 +148,12 @@ __device__ __forceinline__ void heun_nodes(float (&u)[K], float (&m)[K], float (
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const float s = (STIM && ((mask >> j) & 1u)) ? c.gL_uL + c.stim : c.gL_uL;
-    const Deriv f0 = hh_rhs<EXPAPX>(u[j], m[j], h[j], n[j], s, c);
+    const float ma = m[j] + c.m0, ha = h[j] + c.h0, na = n[j] + c.n0;
+    const Deriv f0 = hh_rhs<EXPAPX>(u[j], ma, ha, na, s, c);
     const float u1 = fmaf(dt, f0.u, u[j]);
-    const float m1 = fmaf(-dt, f0.m, m[j]);
-    const float h1 = fmaf(dt, f0.h, h[j]);
-    const float n1 = fmaf(-dt, f0.n, n[j]);
+    const float m1 = fmaf(-dt, f0.m, ma);
+    const float h1 = fmaf(dt, f0.h, ha);
+    const float n1 = fmaf(-dt, f0.n, na);
     // y + dt/2 (f0 + f1) as (y + dt/2 f0) + dt/2 f1: y is then dead once
     // the predictor is formed
     u[j] = fmaf(hdt, f0.u, u[j]);

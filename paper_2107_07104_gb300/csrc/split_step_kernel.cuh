@@ -164,7 +164,8 @@ __device__ __forceinline__ F2 step2(float s, F2 f, F2 y) {
 
 // One Heun substep (eq:heun) of every node a thread holds, on node pairs;
 // y + dt/2 (f0 + f1) is formed as (y + dt/2 f0) + dt/2 f1 like the scalar
-// form, so the two give identical bits.
+// form, so the two give identical bits.  Gates are held as deviations from
+// rest (see heun_nodes).
 template <int K, bool STIM, bool EXPAPX>
 __device__ __forceinline__ void heun_nodes_packed(float (&u)[K], float (&m)[K], float (&h)[K], float (&n)[K],
                                                   const HHConst& c, uint32_t mask) {
@@ -176,9 +177,11 @@ __device__ __forceinline__ void heun_nodes_packed(float (&u)[K], float (&m)[K], 
     const F2 st = mk2(s0, s1);
     const F2 y_u = mk2(u[j], u[j + 1]), y_m = mk2(m[j], m[j + 1]);
     const F2 y_h = mk2(h[j], h[j + 1]), y_n = mk2(n[j], n[j + 1]);
-    const Deriv2 f0 = hh_rhs2<EXPAPX>(y_u, y_m, y_h, y_n, st, c);
-    const F2 v_u = step2(dt, f0.u, y_u), v_m = step2(-dt, f0.m, y_m);
-    const F2 v_h = step2(dt, f0.h, y_h), v_n = step2(-dt, f0.n, y_n);
+    // absolute gates for the right-hand sides and the predictor
+    const F2 a_m = add2(y_m, sp2(c.m0)), a_h = add2(y_h, sp2(c.h0)), a_n = add2(y_n, sp2(c.n0));
+    const Deriv2 f0 = hh_rhs2<EXPAPX>(y_u, a_m, a_h, a_n, st, c);
+    const F2 v_u = step2(dt, f0.u, y_u), v_m = step2(-dt, f0.m, a_m);
+    const F2 v_h = step2(dt, f0.h, a_h), v_n = step2(-dt, f0.n, a_n);
     const F2 p_u = step2(hdt, f0.u, y_u), p_m = step2(-hdt, f0.m, y_m);
     const F2 p_h = step2(hdt, f0.h, y_h), p_n = step2(-hdt, f0.n, y_n);
     const Deriv2 f1 = hh_rhs2<EXPAPX>(v_u, v_m, v_h, v_n, st, c);
@@ -354,7 +357,7 @@ __device__ __forceinline__ void list_network_nodes(const StepArgs& a, const floa
   uint32_t netm = 0;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    const float raw[5] = {u[j], m[j], h[j], n[j], ((mask >> j) & 1u) ? sfrac : 0.0f};
+    const float raw[5] = {u[j], m[j] + a.hh.m0, h[j] + a.hh.h0, n[j] + a.hh.n0, ((mask >> j) & 1u) ? sfrac : 0.0f};
     if (j < nreal && !sur_plain(a, raw)) netm |= 1u << j;
   }
   const int cnt = __popc(netm);
@@ -384,9 +387,9 @@ __device__ __forceinline__ void list_network_nodes(const StepArgs& a, const floa
     if ((netm >> j) & 1u) {
       L[pos] = __int_as_float((int)(base + j));
       L[a.sur_cap + pos] = u[j];
-      L[2 * a.sur_cap + pos] = m[j];
-      L[3 * a.sur_cap + pos] = h[j];
-      L[4 * a.sur_cap + pos] = n[j];
+      L[2 * a.sur_cap + pos] = m[j] + a.hh.m0;  // absolute gates: the network's inputs
+      L[3 * a.sur_cap + pos] = h[j] + a.hh.h0;
+      L[4 * a.sur_cap + pos] = n[j] + a.hh.n0;
       L[5 * a.sur_cap + pos] = ((mask >> j) & 1u) ? sfrac : 0.0f;
       ++pos;
     }
@@ -584,10 +587,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
     for (int j = 0; j < K; ++j) {
       if (j < nreal) {
         const float Vo = s_keep[(0 * K + j) * B + tid] + a.vrest, Vn = u[j] + a.vrest;
+        // gates are held as deviations from rest: differences are the same,
+        // the relative scale is the absolute gate
         const float mo = s_keep[(1 * K + j) * B + tid], ho = s_keep[(2 * K + j) * B + tid];
         const float no = s_keep[(3 * K + j) * B + tid];
-        eq = eq && fabsf(Vn - Vo) <= a.eq_tol * fabsf(Vo) && fabsf(m[j] - mo) <= a.eq_tol * fabsf(mo) &&
-             fabsf(h[j] - ho) <= a.eq_tol * fabsf(ho) && fabsf(n[j] - no) <= a.eq_tol * fabsf(no);
+        eq = eq && fabsf(Vn - Vo) <= a.eq_tol * fabsf(Vo) && fabsf(m[j] - mo) <= a.eq_tol * fabsf(mo + a.hh.m0) &&
+             fabsf(h[j] - ho) <= a.eq_tol * fabsf(ho + a.hh.h0) && fabsf(n[j] - no) <= a.eq_tol * fabsf(no + a.hh.n0);
       }
     }
     const bool warp_eq = __all_sync(0xffffffffu, eq);

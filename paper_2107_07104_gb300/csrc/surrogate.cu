@@ -336,15 +336,17 @@ __device__ __forceinline__ void network_tile(const SurArgs& a, const uint16_t* s
     const float b0 = sB[2 * kHid + k0], b1 = sB[2 * kHid + k1];
     float* dst0 = k0 == 0 ? a.u : a.h;
     float* dst1 = k1 == 1 ? a.m : a.n;
+    // the listed state is absolute; the arrays hold gates as deviations from rest
+    const float off0 = a.rest[k0], off1 = a.rest[k1];
     if (ok0) {
       const int64_t q = sq[r0];
-      dst0[q] = sy[r0 * 4 + k0] + fmaf(o[0] + b0, a.out_sigma[k0], a.out_mu[k0]);
-      dst1[q] = sy[r0 * 4 + k1] + fmaf(o[1] + b1, a.out_sigma[k1], a.out_mu[k1]);
+      dst0[q] = (sy[r0 * 4 + k0] + fmaf(o[0] + b0, a.out_sigma[k0], a.out_mu[k0])) - off0;
+      dst1[q] = (sy[r0 * 4 + k1] + fmaf(o[1] + b1, a.out_sigma[k1], a.out_mu[k1])) - off1;
     }
     if (ok1) {
       const int64_t q = sq[r1];
-      dst0[q] = sy[r1 * 4 + k0] + fmaf(o[2] + b0, a.out_sigma[k0], a.out_mu[k0]);
-      dst1[q] = sy[r1 * 4 + k1] + fmaf(o[3] + b1, a.out_sigma[k1], a.out_mu[k1]);
+      dst0[q] = (sy[r1 * 4 + k0] + fmaf(o[2] + b0, a.out_sigma[k0], a.out_mu[k0])) - off0;
+      dst1[q] = (sy[r1 * 4 + k1] + fmaf(o[3] + b1, a.out_sigma[k1], a.out_mu[k1])) - off1;
     }
   }
 }

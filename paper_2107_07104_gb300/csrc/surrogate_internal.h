@@ -38,6 +38,7 @@ struct SurArgs {
   unsigned long long* fallback_count;
   float in_mu[kIn], in_inv_sigma[kIn];
   float out_mu[kOut], out_sigma[kOut];
+  float rest[kOut];             // 0, m0, h0, n0: the state arrays hold gates minus their rest values
 };
 
 size_t sur_smem_bytes();

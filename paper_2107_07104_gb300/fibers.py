@@ -38,7 +38,8 @@ EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_s
             "fibers_kernel_launches", "fibers_last_error", "fibers_destroy", "fibers_load_surrogate",
             "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward", "fibers_adam_step",
             "fibers_feature_stats", "fibers_adaptive_stats", "fibers_solver_tables", "fibers_emg_create",
-            "fibers_emg_vm3d", "fibers_emg_phi_e", "fibers_emg_nodes", "fibers_emg_last_error", "fibers_emg_destroy")
+            "fibers_emg_vm3d", "fibers_emg_phi_e", "fibers_emg_nodes", "fibers_emg_last_error", "fibers_emg_destroy",
+            "fibers_rest_state")
 SUR_N_PARAMS = 17796
 SUR_BLOB_FLOATS = 3 + 5 + 5 + 4 + 4 + 5 + 5 + 5 + 5 + SUR_N_PARAMS
 SUR_WORK_PER_SAMPLE = 848
@@ -125,6 +126,7 @@ def load(build_if_missing: bool = True):
         L.fibers_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, f32, vp]
         L.fibers_feature_stats.argtypes = [vp, i64, i32, f64p, vp]
         L.fibers_solver_tables.argtypes = [i32, ctypes.c_double, i32, i32, P(i32), P(i32), f64p, f64p]
+        L.fibers_rest_state.argtypes = [P(FibParams), P(ctypes.c_float)]
         L.fibers_emg_create.argtypes = [vp, f64p, ctypes.c_double, P(FibMesh3D), P(vp)]
         L.fibers_emg_vm3d.argtypes = [vp, vp, sz, i32]
         L.fibers_emg_phi_e.argtypes = [vp, vp, sz, i32, ctypes.c_double, i32, P(i32), f64p]
@@ -409,6 +411,15 @@ def fibers_emg_nodes(emg) -> int:
 def fibers_emg_destroy(emg) -> None:
     if emg:
         load().fibers_emg_destroy(emg)
+
+
+def fibers_rest_state(params: dict, mode: int = FIB_MODE_FP32) -> np.ndarray:
+    """(Vrest, m0, h0, n0) the library uses (floats); the state's gate blocks
+    are deviations from these."""
+    out = np.zeros(4, np.float32)
+    pv = make_params(params, mode)
+    _check(load().fibers_rest_state(ctypes.byref(pv), _ptr(out, ctypes.c_float)), None)
+    return out
 
 
 def fibers_kernel_launches(ctx) -> int:

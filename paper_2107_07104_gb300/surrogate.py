@@ -43,6 +43,8 @@ def sample_states(w, n_samples: int, checkpoints: Iterable[int], seed: int, acti
     gen.manual_seed(seed)
     total = w.total_nodes
     state = torch.empty(4 * total, dtype=torch.float32, device=device)
+    # the library's state holds gates as deviations from rest
+    rest = torch.as_tensor(F.fibers_rest_state(w.params), device=device)
     out = []
     with F.Fibers.from_workload(w) as fib:
         done = 0
@@ -51,7 +53,7 @@ def sample_states(w, n_samples: int, checkpoints: Iterable[int], seed: int, acti
             done = c
             F.fibers_read_state(fib.ctx, state)
             s = state.view(4, total)
-            u, m, h, n = s[0], s[1], s[2], s[3]
+            u, m, h, n = s[0], s[1] + rest[1], s[2] + rest[2], s[3] + rest[3]
             # activity: distance from rest in voltage and gates
             act = u.abs() + 50.0 * ((m - m.median()).abs() + (h - h.median()).abs() + (n - n.median()).abs())
             active = torch.nonzero(act > 0.05).flatten()
@@ -92,10 +94,10 @@ def make_dataset(params: dict, states: "torch.Tensor", seed: int, stim_fraction:
 
 
 def rest_state(params: dict) -> np.ndarray:
-    """(u, m, h, n) at rest as the library initialises it (read back, not recomputed)."""
-    with F.Fibers(params, [1], [-1], [0]) as f:
-        st = f.read_state()
-    return st.astype(np.float64)
+    """(u, m, h, n) at rest as the library initialises it (u = 0, the
+    library's resting gates)."""
+    r = F.fibers_rest_state(params).astype(np.float64)
+    return np.array([0.0, r[1], r[2], r[3]])
 
 
 def quiet_box(params: dict, du: float = 8.0, dg: float = 0.03):

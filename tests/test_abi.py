@@ -103,3 +103,20 @@ def test_null_context_is_safe(lib):
     assert lib.fibers_kernel_launches(None) == 0
     assert lib.step(None, 1) == F.FIB_EINVAL
     assert lib.fibers_synchronize(None) == F.FIB_EINVAL
+
+
+def test_rest_state_matches_the_oracle_rest_gates(lib):
+    # host-only call: the library's resting gates (the offsets of the state's
+    # gate blocks) are the steady-state gates of the HH rates at Vrest
+    import oracle
+    p = dict(W.DEFAULT_PARAMS)
+    r = F.fibers_rest_state(p)
+    assert r[0] == np.float32(p["Vrest"])
+    g = oracle.gates_inf(p, p["Vrest"])
+    assert np.allclose(r[1:].astype(np.float64), g, rtol=1.2e-7, atol=0.0)
+    pa = dict(p, exp_approx=1)
+    ra = F.fibers_rest_state(pa)
+    ga = oracle.gates_inf(dict(pa), pa["Vrest"])
+    assert np.allclose(ra[1:].astype(np.float64), ga, rtol=1.2e-7, atol=0.0)
+    with pytest.raises(F.FibersError):
+        F.fibers_rest_state(dict(p, dt_split=-1.0))
