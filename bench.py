@@ -322,7 +322,7 @@ def run_gpu(args, world, rank, local, dist):
     stream = torch.cuda.Stream(device=dev)
     tuning = dict(nodes_per_thread=args.nodes_per_thread, warps_per_cta=args.warps_per_cta,
                   steps_per_launch=S, graph_steps=S, reaction_pairs=args.reaction_pairs,
-                  ctas_per_sm=args.ctas_per_sm)
+                  ctas_per_sm=args.ctas_per_sm, warp_roles=args.warp_roles)
 
     def barrier():
         if dist is not None:
@@ -732,6 +732,8 @@ def main():
     ap.add_argument("--warps-per-cta", type=int, default=0)
     ap.add_argument("--reaction-pairs", type=int, default=0, help="1 scalar, 2 packed FP32x2, 0 auto")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="register budget: 2, 3 or 4 CTAs per SM, 0 auto")
+    ap.add_argument("--warp-roles", type=int, default=0,
+                    help="1 fused step kernel, 2 split reaction/diffusion warps, 0 auto")
     ap.add_argument("--cpu-fibers", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -137,6 +137,13 @@ typedef struct {
   int32_t ctas_per_sm;       /* register budget of the step kernel, as CTAs of 256 threads per
                                 SM: 2 (up to 128 registers per thread), 3 (up to 80) or 4 (up to
                                 64, more warps per SM, a few spills at K = 8); 0: automatic */
+  int32_t warp_roles;        /* 1: every warp of a fiber runs both the reaction and the diffusion
+                                solve (the fused kernel); 2: split roles, with 12 reaction warps
+                                (4 nodes per lane) and 4 diffusion warps (12 nodes per lane)
+                                per CTA of two fibers held in shared memory, for fibers of at
+                                most 1536 nodes in FIB_MODE_FP32 with no flags, Strang 1D-0D-1D
+                                and Crank-Nicolson (nodes_per_thread, warps_per_cta,
+                                reaction_pairs and ctas_per_sm then do not apply); 0: automatic */
 } fib_tuning;
 
 /* Creates a context for n_fibers fibers and copies the inputs to the device.
@@ -246,7 +253,8 @@ fib_status fibers_adaptive_stats(fib_ctx* ctx, int64_t* skipped_fiber_steps);
 
 /* Waits for all enqueued work and reports device-side errors: FIB_ENONFINITE
  * (state became NaN/Inf), FIB_ESTATE (surrogate node list overflowed),
- * FIB_ECUDA.  Thesis: the point of synchronisation between blocks of GPU
+ * FIB_ETIMEOUT (with split warp roles, a bounded wait between the reaction
+ * and diffusion warps gave up; the state is unreliable), FIB_ECUDA.  Thesis: the point of synchronisation between blocks of GPU
  * timesteps (section "Code Generation for GPUs"). */
 fib_status fibers_synchronize(fib_ctx* ctx);
 

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libfibers.so")
 SOURCES = ["split_step.cu", "split_step_expapx.cu", "split_step_adaptive.cu", "fibers_api.cu", "solver_tables.cpp",
-           "read_vm_static.cu", "surrogate.cu", "emg.cu"]
+           "read_vm_static.cu", "surrogate.cu", "emg.cu", "split_step_ws.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -44,6 +44,7 @@ struct fib_ctx {
 
   // layout-dependent device data
   int K = 0, W = 0, n_ctas = 0, levels = 0, rec_stride = 0;
+  bool ws = false;  // split warp roles (split_step_ws.cu)
   int64_t slots_total = 0;
   float* d_state = nullptr;  // 4 * slots_total
   FiberDesc* d_fibers = nullptr;
@@ -224,6 +225,9 @@ int auto_K(const std::vector<int32_t>& n_nodes) {
 
 int auto_W(int w_max) { return w_max * std::max(1, kMaxWarpsPerCta / w_max); }
 
+// Whether the automatic shape uses split warp roles where they apply.
+constexpr bool kWsAuto = false;
+
 void free_layout(fib_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
@@ -236,9 +240,80 @@ void free_layout(fib_ctx* c) {
   dfree(c->d_sur_count);
 }
 
+// Can the split-role kernel run this context?  Plain FP32, no flags,
+// Strang 1D-0D-1D with Crank-Nicolson, every fiber within its slot.
+bool ws_eligible(const fib_ctx* c) {
+  return c->p.mode == FIB_MODE_FP32 && c->p.flags == 0 && c->p.splitting == FIB_SPLIT_STRANG_1D0D1D &&
+         c->p.diffusion == FIB_DIFFUSION_CRANK_NICOLSON && c->n_fibers > 0 && c->max_n <= kWsSlot;
+}
+
+// Layout of the split-role kernel: slots of kWsSlot nodes, two fibers per
+// CTA, solver tables for 12 nodes per diffusion thread (128 threads).
+fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t) {
+  constexpr int KC = 12;
+  std::map<int32_t, int> cls;
+  std::vector<int32_t> lens, tw;
+  for (int32_t n : c->n_nodes)
+    if (!cls.count(n)) {
+      cls[n] = (int)lens.size();
+      lens.push_back(n);
+      tw.push_back(kWsSlot / KC);
+    }
+  SolverTables tab;
+  if (!build_solver_tables(KC, c->r, lens, tw, false, &tab))
+    return fail(c, FIB_EINVAL, "tridiagonal tables: zero pivot (r = %g)", c->r);
+  std::vector<FiberDesc> fd(c->n_fibers);
+  for (int32_t f = 0; f < c->n_fibers; ++f) {
+    const int ci = cls[c->n_nodes[f]];
+    fd[f].slot = (int64_t)f * kWsSlot;
+    fd[f].coff = c->coff[f];
+    fd[f].rec = tab.class_rec[ci];
+    fd[f].n = c->n_nodes[f];
+    fd[f].junction = c->junction[f];
+    fd[f].mu = c->mu[f];
+    fd[f].last_set = (int32_t)tab.class_last[ci];
+    fd[f].slot_len = kWsSlot;
+    fd[f].pad = 0;
+  }
+  const int64_t slot = (int64_t)c->n_fibers * kWsSlot;
+  free_layout(c);
+  c->ws = true;
+  c->K = KC;
+  c->W = 16;
+  c->n_ctas = (c->n_fibers + 1) / 2;
+  c->levels = tab.levels;
+  c->rec_stride = tab.rec_stride;
+  c->slots_total = slot;
+  c->tune.nodes_per_thread = 0;
+  c->tune.warps_per_cta = 16;
+  c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
+  c->tune.graph_steps = t.graph_steps;
+  c->tune.reaction_pairs = 2;
+  c->tune.ctas_per_sm = 2;
+  c->tune.warp_roles = 2;
+  CU(c, cudaMalloc(&c->d_state, sizeof(float) * 4 * (size_t)slot));
+  CU(c, cudaMalloc(&c->d_fibers, sizeof(FiberDesc) * fd.size()));
+  CU(c, cudaMalloc(&c->d_warps, sizeof(WarpMap)));
+  CU(c, cudaMalloc(&c->d_rows, 4 * tab.rows.size()));
+  CU(c, cudaMalloc(&c->d_recs, 4 * std::max<size_t>(tab.recs.size(), 1)));
+  CU(c, cudaMemcpy(c->d_fibers, fd.data(), sizeof(FiberDesc) * fd.size(), cudaMemcpyHostToDevice));
+  std::vector<float> rf(tab.rows.begin(), tab.rows.end()), cf(tab.recs.begin(), tab.recs.end());
+  CU(c, cudaMemcpy(c->d_rows, rf.data(), 4 * rf.size(), cudaMemcpyHostToDevice));
+  if (!cf.empty()) CU(c, cudaMemcpy(c->d_recs, cf.data(), 4 * cf.size(), cudaMemcpyHostToDevice));
+  return FIB_OK;
+}
+
 // Builds the padded layout, CTA packing and solver tables for tuning t.
 // Allocates (uninitialised) state; the caller fills it.
 fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
+  if (t.warp_roles < 0 || t.warp_roles > 2) return fail(c, FIB_EINVAL, "warp_roles must be 0, 1 or 2");
+  if (t.warp_roles == 2 && !ws_eligible(c))
+    return fail(c, FIB_EINVAL,
+                "split warp roles need FIB_MODE_FP32 with no flags, Strang 1D-0D-1D, Crank-Nicolson and fibers of "
+                "at most %d nodes", kWsSlot);
+  if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
+  if (t.warp_roles == 2 || (t.warp_roles == 0 && kWsAuto && t.nodes_per_thread == 0 && ws_eligible(c)))
+    return build_layout_ws(c, t);
   int K = t.nodes_per_thread ? t.nodes_per_thread : auto_K(c->n_nodes);
   if (K != 4 && K != 8 && K != 12 && K != 16) return fail(c, FIB_EINVAL, "nodes_per_thread must be 4, 8, 12 or 16");
   int w_max = 1;
@@ -317,6 +392,8 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   }
 
   free_layout(c);
+  c->ws = false;
+  c->tune.warp_roles = 1;
   c->K = K;
   c->W = W;
   c->n_ctas = n_ctas;
@@ -444,6 +521,7 @@ StepArgs make_args(fib_ctx* c) {
   a.skipped = c->d_skipped;
   a.eq_tol = 1e-5f;
   a.vrest = (float)c->p.Vrest;
+  a.n_fib = c->n_fibers;
   return a;
 }
 
@@ -456,8 +534,9 @@ fib_status enqueue_launches(fib_ctx* c, cudaStream_t s, int64_t offset0, int64_t
   for (int64_t done = 0; done < n; done += S) {
     a.step_offset = offset0 + done;
     a.n_steps = (int32_t)std::min<int64_t>(S, n - done);
-    fib_status st = check_launch(c, launch_split_step(c->K, c->p.mode == FIB_MODE_FP64_THOMAS, a, c->n_ctas, s),
-                                 "split step");
+    const int e = c->ws ? launch_split_step_ws(a, c->n_ctas, s)
+                        : launch_split_step(c->K, c->p.mode == FIB_MODE_FP64_THOMAS, a, c->n_ctas, s);
+    fib_status st = check_launch(c, e, "split step");
     if (st != FIB_OK) return st;
     ++c->launches;
   }
@@ -497,6 +576,8 @@ fib_status build_graph(fib_ctx* c) {
 fib_status check_flag(fib_ctx* c) {
   int32_t flag = 0;
   CU(c, cudaMemcpy(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  if (flag & 4)
+    return fail(c, FIB_ETIMEOUT, "a bounded wait between the reaction and diffusion warps gave up; state unreliable");
   if (flag & 2) return fail(c, FIB_ESTATE, "surrogate network-node list overflowed; its entries were dropped");
   if (flag & 1) return fail(c, FIB_ENONFINITE, "state became non-finite (NaN/Inf)");
   return FIB_OK;
@@ -699,7 +780,7 @@ fib_status fibers_create(const fib_params* p, int32_t n_fibers, const int32_t* n
   // Reserve read_vm_static's staging array on this device now (a failure
   // here is not an error of this call: read_vm_static tries again).
   if (fib::prepare_static_stage(cx->device) != 0) cudaGetLastError();
-  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000, 0, 0};
+  fib_tuning t = tuning ? *tuning : fib_tuning{0, 0, 0, 1000, 0, 0, 0};
   st = build_layout(cx, t);
   if (st == FIB_OK) {
     if ((e = cudaStreamCreateWithFlags(&cx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -987,6 +1068,7 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
   fib_tuning win = start;
   float win_ms = -1.0f;
   fib_status result = FIB_OK;
+  std::vector<fib_tuning> cands;
   for (int K : {8, 12, 16}) {
     int w_max = 1;
     for (int32_t n : c->n_nodes) w_max = std::max(w_max, warps_for(n, K));
@@ -994,28 +1076,33 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
     std::vector<int> Ws{auto_W(w_max)};
     if (w_max * 2 <= kMaxWarpsPerCta && auto_W(w_max) != w_max) Ws.push_back(w_max);
     for (int W : Ws)
-     for (int pairs : {1, 2})
-      for (int occ : {2, 3, 4}) {
-      fib_tuning t{K, W, start.steps_per_launch, start.graph_steps, pairs, occ};
-      if (build_layout(c, t) != FIB_OK) continue;
-      if (need > 0 && scatter_state(c, keep) != FIB_OK) continue;
-      StepArgs a = make_args(c);
-      a.step_offset = 0;
-      a.n_steps = n_trial_steps;
-      const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
-      // one warm-up launch, then the timed one
-      launch_split_step(c->K, fp64, a, c->n_ctas, c->stream);
-      cudaEventRecord(e0, c->stream);
-      int le = launch_split_step(c->K, fp64, a, c->n_ctas, c->stream);
-      cudaEventRecord(e1, c->stream);
-      c->launches += 2;
-      if (le != 0 || cudaEventSynchronize(e1) != cudaSuccess) continue;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (win_ms < 0 || ms < win_ms) {
-        win_ms = ms;
-        win = c->tune;
-      }
+      for (int pairs : {1, 2})
+        for (int occ : {2, 3, 4}) cands.push_back(fib_tuning{K, W, start.steps_per_launch, start.graph_steps, pairs, occ, 1});
+  }
+  if (ws_eligible(c)) cands.push_back(fib_tuning{0, 0, start.steps_per_launch, start.graph_steps, 0, 0, 2});
+  for (const fib_tuning& t : cands) {
+    if (build_layout(c, t) != FIB_OK) continue;
+    if (need > 0 && scatter_state(c, keep) != FIB_OK) continue;
+    StepArgs a = make_args(c);
+    a.step_offset = 0;
+    a.n_steps = n_trial_steps;
+    const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
+    auto launch = [&]() {
+      return c->ws ? launch_split_step_ws(a, c->n_ctas, c->stream)
+                   : launch_split_step(c->K, fp64, a, c->n_ctas, c->stream);
+    };
+    // one warm-up launch, then the timed one
+    launch();
+    cudaEventRecord(e0, c->stream);
+    int le = launch();
+    cudaEventRecord(e1, c->stream);
+    c->launches += 2;
+    if (le != 0 || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (win_ms < 0 || ms < win_ms) {
+      win_ms = ms;
+      win = c->tune;
     }
   }
   cudaEventDestroy(e0);

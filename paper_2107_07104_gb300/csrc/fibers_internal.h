@@ -22,6 +22,9 @@ constexpr int kRecPerLevel = 3;
 constexpr int kMaxFibersPerCta = 15;  // named barriers 1..15 (0 is __syncthreads)
 constexpr int kMaxWarpsPerCta = 8;    // 256 threads: the kernels' launch bound
 constexpr int kMaxLevels = 12;
+// Slot (nodes) of a fiber in the split-role layout (split_step_ws.cu):
+// 12 reaction warps x 32 lanes x 4 nodes = 4 diffusion warps x 32 x 12.
+constexpr int kWsSlot = 1536;
 
 struct FiberDesc {
   int64_t slot;      // index of node 0 in the padded state arrays
@@ -69,7 +72,8 @@ struct StepArgs {
   const int64_t* mu_off;   // [n_mu + 1]
   const int64_t* fire_k;   // firing substep index, sorted within each MU
   const int64_t* step_base;  // device-resident index of the next split step
-  int32_t* flag;           // bit 0: non-finite state seen; bit 1: surrogate node list overflowed
+  int32_t* flag;           // bit 0: non-finite state seen; bit 1: surrogate node list overflowed;
+                           // bit 2: a bounded wait between warp roles gave up
   HHConst hh;
   double r;                // tridiagonal-table parameter: c dt_1d / h^2 (CN), 2 c dt_1d / h^2 (IE)
   int64_t step_offset;     // this launch starts at *step_base + step_offset
@@ -106,6 +110,7 @@ struct StepArgs {
   float sur_env_lo[5], sur_env_hi[5], sur_quiet_lo[5], sur_quiet_hi[5];
   float inv_n_sub;
   float vrest;             // resting potential (the test uses V = u + Vrest)
+  int32_t n_fib;           // fibers of the context (split-role kernel: two per CTA)
 };
 
 // Host-built solver tables for one (K, r, fiber-length set).
@@ -132,6 +137,10 @@ int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, voi
 // (split_step_adaptive.cu).
 int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream);
 int launch_split_step_adaptive(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
+// Split roles (split_step_ws.cu): reaction and diffusion warps, two fibers
+// of at most kWsSlot nodes per CTA, tables for K = 12.
+int launch_split_step_ws(const StepArgs& a, int n_ctas, void* stream);
+size_t split_step_ws_smem_bytes();
 // Surrogate mode's split step (one per launch) with the network-node list
 // (surrogate.cu).
 int launch_split_step_sur(int K, const StepArgs& a, int n_ctas, void* stream);

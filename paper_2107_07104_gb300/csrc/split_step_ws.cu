@@ -1,0 +1,280 @@
+// Split step with dedicated reaction and diffusion warps (plain FP32,
+// Strang 1D-0D-1D with Crank-Nicolson: eq:monodomain_strang,
+// eq:lumping_crank_nicolson_2, eq:heun), for fibers of at most kWsSlot
+// nodes.
+//
+// The fused kernel (split_step_kernel.cuh) gives every warp of a fiber both
+// the reaction and the diffusion solve.  The solve couples the fiber's
+// warps, so each of its exchanges waits at a fiber barrier for the slowest
+// warp, and the warps of a fiber drift apart over the long reaction phase.
+// Here the two jobs go to different warps of one CTA, which owns two fibers
+// whose state lives in shared memory for a whole launch:
+//   * 12 reaction warps hold 4 nodes per lane and run the Heun substeps of
+//     one fiber while
+//   * 4 diffusion warps (12 nodes per lane) run the two Crank-Nicolson
+//     halves between that fiber's reactions on the other fiber,
+// so the fibers alternate: reaction(A) | solve(B), reaction(B) | solve(A).
+// The roles hand fibers over through shared-memory mbarriers: a reaction
+// warp waits only until the diffusion warps have released the fiber it is
+// about to integrate (one slot earlier), never for the other reaction
+// warps.  Every wait is bounded; a wait that gives up sets bit 2 of the
+// error flag, and the kernel finishes with its state unreliable instead of
+// hanging.  Results equal the fused kernel's up to rounding order
+// (the same reaction arithmetic; the solve at 12 nodes per thread).
+#include "split_step_kernel.cuh"
+
+namespace fib {
+namespace {
+
+constexpr int kWsReactWarps = 12;
+constexpr int kWsCnWarps = 4;
+constexpr int kWsThreads = 32 * (kWsReactWarps + kWsCnWarps);
+constexpr int kWsKR = 4;    // nodes per reaction lane
+constexpr int kWsKC = 12;   // nodes per diffusion lane
+constexpr int kWsCnThreads = 32 * kWsCnWarps;
+constexpr int kWsSpin = 1 << 20;  // try_wait rounds before a wait gives up
+static_assert(32 * kWsReactWarps * kWsKR == kWsSlot, "reaction warps cover the slot");
+static_assert(kWsCnThreads * kWsKC == kWsSlot, "diffusion warps cover the slot");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+               : "memory");
+}
+// Waits for the phase of the given parity to complete; gives up after a
+// bounded number of rounds (then sets bit 2 of *flag and every later wait
+// of this thread returns at once).
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int32_t* flag, bool& abort) {
+  if (abort) return;
+  const uint32_t addr = smem_addr(bar);
+  for (int i = 0; i < kWsSpin; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return;
+  }
+  atomicOr(flag, 4);
+  abort = true;
+}
+
+// Stimulus state of one reaction lane for one fiber (see the fused kernel).
+struct Stim {
+  uint32_t mask;
+  int64_t cur, fend, fk;
+};
+
+__device__ __forceinline__ Stim stim_init(const StepArgs& a, const FiberDesc& fd, int first_node, int64_t step0) {
+  Stim s{0u, 0, 0, INT64_MAX};
+  if (fd.mu < 0 || fd.mu >= a.n_mu) return s;
+  const int lo = max(fd.junction - a.hw, 0), hi = min(fd.junction + a.hw, fd.n - 1);
+#pragma unroll
+  for (int j = 0; j < kWsKR; ++j) {
+    const int i = first_node + j;
+    if (i >= lo && i <= hi) s.mask |= 1u << j;
+  }
+  if (!s.mask) return s;
+  int64_t lo_f = a.mu_off[fd.mu], hi_f = a.mu_off[fd.mu + 1];
+  s.fend = hi_f;
+  const int64_t k0 = step0 * a.n_sub;
+  while (lo_f < hi_f) {
+    const int64_t mid = (lo_f + hi_f) >> 1;
+    if (a.fire_k[mid] + a.pulse <= k0) lo_f = mid + 1;
+    else hi_f = mid;
+  }
+  s.cur = lo_f;
+  if (s.cur < s.fend) s.fk = a.fire_k[s.cur];
+  return s;
+}
+
+__global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // layout: state of 2 fibers (u m h n x kWsSlot each), solve tables and
+  // exchange buffers of the diffusion warps, 4 mbarriers
+  float* st = reinterpret_cast<float*>(smem_raw);                         // [2][4][kWsSlot]
+  float* s_rows = st + 2 * 4 * kWsSlot;                                   // [interior | last A | last B] sets
+  constexpr int set_len = kWsKC * kCoefPerRow;
+  float* s_coef = s_rows + 3 * set_len;                                   // [2][kNumCoef][kStride]
+  Exchange<float> x;
+  x.first = s_coef + 2 * kNumCoef * kStride;
+  x.last = x.first + kStride;
+  x.D = x.last + kStride;
+  x.E = x.D + kStride;
+  x.y = x.E + kStride;
+  x.r2 = x.y + kStride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(x.r2 + 2 * kStride);     // ready_R[2], ready_C[2]
+
+  const int tid = threadIdx.x;
+  const int64_t f0 = 2 * (int64_t)blockIdx.x;
+  const int64_t left = (int64_t)a.n_fib - f0;
+  const int nf = left < 2 ? (int)left : 2;  // fibers of this CTA (1 or 2)
+  FiberDesc fd[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) fd[q] = a.fibers[f0 + (q < nf ? q : 0)];
+
+  // load the state (gates as deviations from rest), tables, barriers
+  for (int q = 0; q < nf; ++q) {
+    for (int v = 0; v < 4; ++v) {
+      const float* src = v == 0 ? a.u : v == 1 ? a.m : v == 2 ? a.h : a.n;
+      const float4* g = reinterpret_cast<const float4*>(src + fd[q].slot);
+      float4* s4 = reinterpret_cast<float4*>(st + (q * 4 + v) * kWsSlot);
+      for (int i = tid; i < kWsSlot / 4; i += kWsThreads) s4[i] = g[i];
+    }
+  }
+  const float* g_rows = static_cast<const float*>(a.rows);
+  for (int i = tid; i < set_len; i += kWsThreads) {
+    s_rows[i] = g_rows[i];
+    for (int q = 0; q < 2; ++q) s_rows[(1 + q) * set_len + i] = g_rows[fd[q].last_set + i];
+  }
+  const float* g_recs = static_cast<const float*>(a.recs);
+  if (tid < 2 * kWsCnThreads) {
+    const int q = tid / kWsCnThreads, p = tid % kWsCnThreads;
+    const float* rec = g_recs + fd[q].rec + (int64_t)p * a.rec_stride;
+    float* cf = s_coef + q * kNumCoef * kStride;
+    for (int k = 0; k < 7; ++k) cf[k * kStride + p] = rec[k];
+    cf[kPKE * kStride + p] = p > 0 ? rec[4 - a.rec_stride] : 0.0f;
+    cf[kPKD * kStride + p] = p > 0 ? rec[5 - a.rec_stride] : 0.0f;
+    cf[kPKDn * kStride + p] = p > 0 ? rec[6 - a.rec_stride] : 0.0f;
+  }
+  if (tid == 0) {
+    mbar_init(&bars[0], kWsCnThreads);  // ready_R[A]: the diffusion warps released fiber A
+    mbar_init(&bars[1], kWsCnThreads);  // ready_R[B]
+    mbar_init(&bars[2], 32 * kWsReactWarps);  // ready_C[A]: the reaction warps released fiber A
+    mbar_init(&bars[3], 32 * kWsReactWarps);  // ready_C[B]
+  }
+  __syncthreads();
+
+  const int64_t step0 = *a.step_base + a.step_offset;
+  const int S = a.n_steps;
+  bool abort = false;
+  const int warp = tid >> 5;
+  if (warp < kWsReactWarps) {
+    // ---- reaction warps: 4 nodes per lane, fibers A, B alternately ----
+    const int q0 = tid;  // nodes [4 q0, 4 q0 + 4)
+    Stim sm[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) sm[q] = stim_init(a, fd[q], kWsKR * q0, step0);
+    for (int s = 0; s < S; ++s) {
+      const int64_t stp = step0 + s;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        mbar_wait(&bars[q], (uint32_t)(s & 1), a.flag, abort);
+        if (q < nf) {
+          float* base = st + q * 4 * kWsSlot + kWsKR * q0;
+          const float4 vu = *reinterpret_cast<const float4*>(base);
+          const float4 vm = *reinterpret_cast<const float4*>(base + kWsSlot);
+          const float4 vh = *reinterpret_cast<const float4*>(base + 2 * kWsSlot);
+          const float4 vn = *reinterpret_cast<const float4*>(base + 3 * kWsSlot);
+          float u[4] = {vu.x, vu.y, vu.z, vu.w}, m[4] = {vm.x, vm.y, vm.z, vm.w};
+          float h[4] = {vh.x, vh.y, vh.z, vh.w}, n[4] = {vn.x, vn.y, vn.z, vn.w};
+          Stim& z = sm[q];
+          for (int k = 0; k < a.n_sub; ++k) {
+            bool on = false;
+            if (z.mask) {
+              const int64_t kk = stp * a.n_sub + k;
+              while (z.fk != INT64_MAX && z.fk + a.pulse <= kk) {
+                ++z.cur;
+                z.fk = z.cur < z.fend ? a.fire_k[z.cur] : INT64_MAX;
+              }
+              on = z.fk <= kk;
+            }
+            if (on) heun_nodes_packed<kWsKR, true, false>(u, m, h, n, a.hh, z.mask);
+            else heun_nodes_packed<kWsKR, false, false>(u, m, h, n, a.hh, z.mask);
+          }
+          *reinterpret_cast<float4*>(base) = make_float4(u[0], u[1], u[2], u[3]);
+          *reinterpret_cast<float4*>(base + kWsSlot) = make_float4(m[0], m[1], m[2], m[3]);
+          *reinterpret_cast<float4*>(base + 2 * kWsSlot) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(base + 3 * kWsSlot) = make_float4(n[0], n[1], n[2], n[3]);
+        }
+        mbar_arrive(&bars[2 + q]);
+      }
+    }
+  } else {
+    // ---- diffusion warps: the Crank-Nicolson halves between reactions ----
+    const int p = tid - 32 * kWsReactWarps;  // chunk [12 p, 12 p + 12)
+    SolveCtx<kWsKC, float> sc[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int Tf = (fd[q].n + kWsKC - 1) / kWsKC;
+      const int nreal = min(max(fd[q].n - p * kWsKC, 0), kWsKC);
+      sc[q].p = p;
+      sc[q].Tw = kWsCnThreads;
+      sc[q].tid = p;
+      sc[q].nreal = nreal;
+      sc[q].bar_id = 1;  // the diffusion warps' own named barrier
+      sc[q].levels = a.n_levels;
+      sc[q].edge = (nreal < kWsKC) || (p == Tf - 1);
+      sc[q].set = s_rows + ((p == Tf - 1) ? (1 + q) * set_len : 0);
+      sc[q].r = fd[q].n > 1 ? (float)a.r : 0.0f;
+      sc[q].ie = false;
+      sc[q].rec = g_recs + fd[q].rec + (int64_t)p * a.rec_stride;
+      sc[q].cf = s_coef + q * kNumCoef * kStride + p;
+    }
+    auto solve = [&](int q, const SolveCtx<kWsKC, float>& scq, int count) {
+      float* ub = st + q * 4 * kWsSlot + kWsKC * p;
+      float u[kWsKC];
+#pragma unroll
+      for (int j = 0; j < kWsKC; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(ub + j);
+        u[j] = v.x; u[j + 1] = v.y; u[j + 2] = v.z; u[j + 3] = v.w;
+      }
+      for (int c = 0; c < count; ++c) cn_solve<kWsKC, float>(u, scq, x);
+#pragma unroll
+      for (int j = 0; j < kWsKC; j += 4)
+        *reinterpret_cast<float4*>(ub + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+    };
+    for (int s = 0; s <= S; ++s) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        // before step s: the second half of step s - 1 (after its reaction)
+        // and the first half of step s
+        if (s > 0) mbar_wait(&bars[2 + q], (uint32_t)((s - 1) & 1), a.flag, abort);
+        const int count = (s > 0 ? a.n_cn : 0) + (s < S ? a.n_cn : 0);
+        if (q < nf) solve(q, sc[q], count);  // all diffusion warps take the same branch
+        if (s < S) mbar_arrive(&bars[q]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // store the state and test it
+  bool finite = true;
+  for (int q = 0; q < nf; ++q) {
+    for (int v = 0; v < 4; ++v) {
+      float* dst = v == 0 ? a.u : v == 1 ? a.m : v == 2 ? a.h : a.n;
+      float4* g = reinterpret_cast<float4*>(dst + fd[q].slot);
+      const float4* s4 = reinterpret_cast<const float4*>(st + (q * 4 + v) * kWsSlot);
+      for (int i = tid; i < kWsSlot / 4; i += kWsThreads) {
+        const float4 w = s4[i];
+        finite = finite && isfinite(w.x) && isfinite(w.y) && isfinite(w.z) && isfinite(w.w);
+        g[i] = w;
+      }
+    }
+  }
+  if (!finite) atomicOr(a.flag, 1);
+}
+
+}  // namespace
+
+size_t split_step_ws_smem_bytes() {
+  return 4 * ((size_t)2 * 4 * kWsSlot + 3 * kWsKC * kCoefPerRow + 2 * kNumCoef * kStride + 7 * kStride) +
+         4 * sizeof(uint64_t) + 16;
+}
+
+int launch_split_step_ws(const StepArgs& a, int n_ctas, void* stream) {
+  if (n_ctas <= 0 || a.n_steps <= 0) return 0;
+  const size_t smem = split_step_ws_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(split_step_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  split_step_ws_kernel<<<n_ctas, kWsThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace fib

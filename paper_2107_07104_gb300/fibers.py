@@ -69,7 +69,7 @@ class FibMesh3D(ctypes.Structure):
 class FibTuning(ctypes.Structure):
     _fields_ = [("nodes_per_thread", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("steps_per_launch", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
-                ("reaction_pairs", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("reaction_pairs", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("warp_roles", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
