@@ -52,9 +52,10 @@ typedef enum {
   FIB_ENOMEM = 2,      /* device or host allocation failed */
   FIB_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
   FIB_ENONFINITE = 4,  /* the state became NaN/Inf; it stays readable */
-  FIB_ETIMEOUT = 5,    /* a bounded host wait gave up */
+  FIB_ETIMEOUT = 5,    /* a bounded wait gave up (on the host, or between a kernel's warps) */
   FIB_ESTATE = 6,      /* call not valid in the current state */
-  FIB_ENOTSUP = 7      /* valid request that the library does not support */
+  FIB_ENOTSUP = 7,     /* valid request that the library does not support */
+  FIB_EIO = 8          /* a file could not be opened, read or written */
 } fib_status;
 
 /* Solve modes. */
@@ -272,8 +273,29 @@ fib_status fibers_set_tuning(fib_ctx* ctx, const fib_tuning* tuning);
  * adaptive skip count so the simulation is unchanged.  best (nullable)
  * receives the choice.  Synchronises.  No thesis counterpart (see
  * fibers_set_tuning).  Errors: FIB_EINVAL (n_trial_steps < 1), FIB_ENOTSUP
- * (surrogate mode, whose step kernel it does not time), FIB_ECUDA. */
+ * (surrogate mode, whose step kernel it does not time), FIB_ECUDA.
+ *
+ * The choice is cached for the process, keyed by the GPU model (name, SM
+ * count, compute capability), the mode, flags, splitting and diffusion
+ * scheme, r = c dt_1D / h^2, the substep counts and the length histogram
+ * (every distinct fiber length with its number of fibers).  A later call on
+ * a context with an equal key applies the cached shape (like
+ * fibers_set_tuning, keeping the context's steps_per_launch and graph_steps)
+ * and launches no trial steps. */
 fib_status fibers_autotune(fib_ctx* ctx, int32_t n_trial_steps, fib_tuning* best);
+
+/* The autotune cache.  size: entries held.  clear: drops them all.  save:
+ * writes every entry to a text file (first line "fibers-autotune-cache 1",
+ * then one line per entry; the layout is described in the implementation).
+ * load: merges a file's entries into the cache (an entry with an equal key
+ * is replaced); nothing is merged unless every line parses.  Host-only, no
+ * thesis counterpart.  Errors: FIB_EINVAL (NULL path, malformed file; the
+ * message names the line), FIB_EIO (file cannot be opened, read or
+ * written); the message is read with fibers_last_error(NULL). */
+int64_t fibers_autotune_cache_size(void);
+fib_status fibers_autotune_cache_clear(void);
+fib_status fibers_autotune_cache_save(const char* path);
+fib_status fibers_autotune_cache_load(const char* path);
 
 /* ---------------------------------------------------------------------------
  * Reaction-step surrogate (FIB_MODE_SURROGATE).
@@ -454,8 +476,8 @@ fib_status fibers_rest_state(const fib_params* p, float* out);
 int64_t fibers_kernel_launches(const fib_ctx* ctx);
 
 /* Message of the last failing call on ctx (never NULL).  With ctx == NULL:
- * the message of the last failed fibers_create on this thread.  No thesis
- * counterpart. */
+ * the message of the last failed call on this thread that had no context
+ * (fibers_create, the autotune cache calls).  No thesis counterpart. */
 const char* fibers_last_error(const fib_ctx* ctx);
 
 /* Frees everything the context owns, after waiting for its stream.  NULL is

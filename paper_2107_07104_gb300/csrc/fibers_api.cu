@@ -13,7 +13,9 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "fibers.h"
@@ -248,16 +250,16 @@ bool ws_eligible(const fib_ctx* c) {
 }
 
 // Layout of the split-role kernel: slots of kWsSlot nodes, two fibers per
-// CTA, solver tables for 12 nodes per diffusion thread (128 threads).
+// CTA, solver tables for kWsKC nodes per diffusion thread.
 fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t) {
-  constexpr int KC = 12;
+  constexpr int KC = kWsKC;
   std::map<int32_t, int> cls;
   std::vector<int32_t> lens, tw;
   for (int32_t n : c->n_nodes)
     if (!cls.count(n)) {
       cls[n] = (int)lens.size();
       lens.push_back(n);
-      tw.push_back(kWsSlot / KC);
+      tw.push_back(kWsCnThreads);
     }
   SolverTables tab;
   if (!build_solver_tables(KC, c->r, lens, tw, false, &tab))
@@ -279,17 +281,17 @@ fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t) {
   free_layout(c);
   c->ws = true;
   c->K = KC;
-  c->W = 16;
+  c->W = kWsWarps;
   c->n_ctas = (c->n_fibers + 1) / 2;
   c->levels = tab.levels;
   c->rec_stride = tab.rec_stride;
   c->slots_total = slot;
   c->tune.nodes_per_thread = 0;
-  c->tune.warps_per_cta = 16;
+  c->tune.warps_per_cta = kWsWarps;
   c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
   c->tune.graph_steps = t.graph_steps;
   c->tune.reaction_pairs = 2;
-  c->tune.ctas_per_sm = 2;
+  c->tune.ctas_per_sm = kWsMinBlocks;
   c->tune.warp_roles = 2;
   CU(c, cudaMalloc(&c->d_state, sizeof(float) * 4 * (size_t)slot));
   CU(c, cudaMalloc(&c->d_fibers, sizeof(FiberDesc) * fd.size()));
@@ -1039,12 +1041,136 @@ fib_status fibers_set_tuning(fib_ctx* c, const fib_tuning* t) {
   return st;
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Autotune cache: the winning launch shape per (GPU model, method switches,
+// r, substeps, length histogram), process-wide under a mutex, with a text
+// file form.  The histogram is every distinct fiber length with its count;
+// contexts with equal keys have identical layouts and identical work, so the
+// stored shape is the one timing would choose again (up to timing noise).
+// ---------------------------------------------------------------------------
+
+struct TuneKey {
+  std::string gpu;  // name, SM count and compute capability
+  int32_t mode = 0, flags = 0, splitting = 0, diffusion = 0;
+  int64_t n_sub = 0, n_cn = 0;
+  double r = 0.0;
+  std::vector<std::pair<int32_t, int64_t>> hist;  // (length, fibers), ascending length
+  bool operator<(const TuneKey& o) const {
+    return std::tie(gpu, mode, flags, splitting, diffusion, n_sub, n_cn, r, hist) <
+           std::tie(o.gpu, o.mode, o.flags, o.splitting, o.diffusion, o.n_sub, o.n_cn, o.r, o.hist);
+  }
+};
+struct TuneChoice {
+  int32_t nodes_per_thread = 0, warps_per_cta = 0, reaction_pairs = 0, ctas_per_sm = 0, warp_roles = 0;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+bool tune_key(const fib_ctx* c, TuneKey* k) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return false;
+  char gpu[320];
+  snprintf(gpu, sizeof(gpu), "%s|%d SMs|sm_%d%d", prop.name, prop.multiProcessorCount, prop.major, prop.minor);
+  for (char* q = gpu; *q; ++q)
+    if (*q == '\t' || *q == '\n') *q = ' ';
+  k->gpu = gpu;
+  k->mode = c->p.mode;
+  k->flags = c->p.flags;
+  k->splitting = c->p.splitting;
+  k->diffusion = c->p.diffusion;
+  k->n_sub = c->n_sub;
+  k->n_cn = c->n_cn;
+  k->r = c->r;
+  std::map<int32_t, int64_t> h;
+  for (int32_t n : c->n_nodes) ++h[n];
+  k->hist.assign(h.begin(), h.end());
+  return true;
+}
+
+// One line per entry, tab-separated fields:
+//   gpu  mode flags splitting diffusion n_sub n_cn r(hex float)
+//   K W pairs occ roles  n_lengths length:count ...
+std::string tune_line(const TuneKey& k, const TuneChoice& v) {
+  std::string s = k.gpu;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "\t%d %d %d %d %lld %lld %a\t%d %d %d %d %d\t%zu", k.mode, k.flags, k.splitting,
+           k.diffusion, (long long)k.n_sub, (long long)k.n_cn, k.r, v.nodes_per_thread, v.warps_per_cta,
+           v.reaction_pairs, v.ctas_per_sm, v.warp_roles, k.hist.size());
+  s += buf;
+  for (const auto& e : k.hist) {
+    snprintf(buf, sizeof(buf), " %d:%lld", e.first, (long long)e.second);
+    s += buf;
+  }
+  return s;
+}
+
+bool parse_tune_line(const std::string& line, TuneKey* k, TuneChoice* v) {
+  const size_t t1 = line.find('\t');
+  if (t1 == std::string::npos || t1 == 0) return false;
+  k->gpu = line.substr(0, t1);
+  const char* q = line.c_str() + t1 + 1;
+  long long n_sub = 0, n_cn = 0;
+  int used = 0;
+  if (sscanf(q, "%d %d %d %d %lld %lld %la%n", &k->mode, &k->flags, &k->splitting, &k->diffusion, &n_sub, &n_cn,
+             &k->r, &used) != 7)
+    return false;
+  k->n_sub = n_sub;
+  k->n_cn = n_cn;
+  q += used;
+  size_t n_len = 0;
+  if (sscanf(q, " %d %d %d %d %d %zu%n", &v->nodes_per_thread, &v->warps_per_cta, &v->reaction_pairs,
+             &v->ctas_per_sm, &v->warp_roles, &n_len, &used) != 6)
+    return false;
+  q += used;
+  if (n_len == 0 || n_len > (1u << 24)) return false;
+  k->hist.clear();
+  int32_t prev = 0;
+  for (size_t i = 0; i < n_len; ++i) {
+    int len = 0;
+    long long cnt = 0;
+    if (sscanf(q, " %d:%lld%n", &len, &cnt, &used) != 2) return false;
+    if (len <= prev || cnt <= 0) return false;  // ascending, positive
+    k->hist.emplace_back(len, (int64_t)cnt);
+    prev = len;
+    q += used;
+  }
+  while (*q == ' ' || *q == '\r') ++q;
+  return *q == 0;
+}
+
+}  // namespace
+
 fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) {
   if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
   if (n_trial_steps < 1) return fail(c, FIB_EINVAL, "n_trial_steps must be >= 1");
   if (c->p.mode == FIB_MODE_SURROGATE)
     return fail(c, FIB_ENOTSUP, "autotune times the plain step kernel, which surrogate mode does not run");
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  TuneKey key;
+  const bool keyed = tune_key(c, &key);
+  if (keyed) {
+    TuneChoice hit;
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        hit = it->second;
+        found = true;
+      }
+    }
+    if (found) {
+      // the cached shape, keeping this context's launch lengths
+      const fib_tuning t{hit.nodes_per_thread, hit.warps_per_cta, c->tune.steps_per_launch, c->tune.graph_steps,
+                         hit.reaction_pairs, hit.ctas_per_sm, hit.warp_roles};
+      if (fibers_set_tuning(c, &t) == FIB_OK) {
+        if (best) *best = c->tune;
+        return FIB_OK;
+      }
+    }
+  }
   const size_t need = 4 * (size_t)c->total;
   const int64_t step_keep = c->next_step;
   // the trial launches of adaptive mode count skipped fiber-steps; keep the
@@ -1122,7 +1248,73 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
   c->next_step = step_keep;
   if (best) *best = c->tune;
   if (win_ms < 0 && result == FIB_OK) result = fail(c, FIB_ECUDA, "autotune: no candidate ran");
+  if (result == FIB_OK && keyed) {
+    const TuneChoice v{c->tune.nodes_per_thread, c->tune.warps_per_cta, c->tune.reaction_pairs, c->tune.ctas_per_sm,
+                       c->tune.warp_roles};
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = v;
+  }
   return result;
+}
+
+int64_t fibers_autotune_cache_size(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return (int64_t)g_tune_cache.size();
+}
+
+fib_status fibers_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.clear();
+  return FIB_OK;
+}
+
+fib_status fibers_autotune_cache_save(const char* path) {
+  if (!path) return fail(nullptr, FIB_EINVAL, "path is NULL");
+  std::string text = "fibers-autotune-cache 1\n";
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& e : g_tune_cache) text += tune_line(e.first, e.second) + "\n";
+  }
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(nullptr, FIB_EIO, "cannot open %s for writing", path);
+  const bool ok = fwrite(text.data(), 1, text.size(), f) == text.size();
+  if (fclose(f) != 0 || !ok) return fail(nullptr, FIB_EIO, "cannot write %s", path);
+  return FIB_OK;
+}
+
+fib_status fibers_autotune_cache_load(const char* path) {
+  if (!path) return fail(nullptr, FIB_EINVAL, "path is NULL");
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(nullptr, FIB_EIO, "cannot open %s", path);
+  std::string text;
+  char buf[65536];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  const bool read_ok = !ferror(f);
+  fclose(f);
+  if (!read_ok) return fail(nullptr, FIB_EIO, "cannot read %s", path);
+  std::vector<std::pair<TuneKey, TuneChoice>> entries;
+  size_t pos = 0, line_no = 0;
+  while (pos < text.size()) {
+    size_t end = text.find('\n', pos);
+    if (end == std::string::npos) end = text.size();
+    const std::string line = text.substr(pos, end - pos);
+    pos = end + 1;
+    ++line_no;
+    if (line_no == 1) {
+      if (line != "fibers-autotune-cache 1") return fail(nullptr, FIB_EINVAL, "%s: not an autotune cache file", path);
+      continue;
+    }
+    if (line.empty()) continue;
+    TuneKey k;
+    TuneChoice v;
+    if (!parse_tune_line(line, &k, &v)) return fail(nullptr, FIB_EINVAL, "%s:%zu: malformed entry", path, line_no);
+    entries.emplace_back(std::move(k), v);
+  }
+  if (line_no == 0) return fail(nullptr, FIB_EINVAL, "%s: empty file", path);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : entries) g_tune_cache[std::move(e.first)] = e.second;
+  return FIB_OK;
 }
 
 int64_t fibers_kernel_launches(const fib_ctx* c) { return c ? c->launches : 0; }

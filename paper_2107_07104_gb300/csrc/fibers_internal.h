@@ -22,9 +22,21 @@ constexpr int kRecPerLevel = 3;
 constexpr int kMaxFibersPerCta = 15;  // named barriers 1..15 (0 is __syncthreads)
 constexpr int kMaxWarpsPerCta = 8;    // 256 threads: the kernels' launch bound
 constexpr int kMaxLevels = 12;
-// Slot (nodes) of a fiber in the split-role layout (split_step_ws.cu):
-// 12 reaction warps x 32 lanes x 4 nodes = 4 diffusion warps x 32 x 12.
+// Shape of the split-role kernel (split_step_ws.cu): a fiber's slot of
+// kWsSlot nodes is covered by kWsReactWarps reaction warps of kWsKR nodes
+// per lane, and by the diffusion warps at kWsKC nodes per lane; a CTA holds
+// two fibers and kWsMinBlocks CTAs share an SM.
 constexpr int kWsSlot = 1536;
+constexpr int kWsReactWarps = 12;
+constexpr int kWsKR = 4;
+constexpr int kWsKC = 12;
+constexpr int kWsMinBlocks = 2;
+constexpr int kWsCnThreads = kWsSlot / kWsKC;
+constexpr int kWsWarps = kWsReactWarps + kWsCnThreads / 32;
+static_assert(32 * kWsReactWarps * kWsKR == kWsSlot, "reaction warps cover the slot");
+static_assert(kWsCnThreads * kWsKC == kWsSlot && kWsCnThreads % 32 == 0, "diffusion warps cover the slot");
+static_assert(kWsKR % 4 == 0 && kWsKC % 4 == 0, "slot rows move as float4");
+static_assert(kWsReactWarps * 32 >= kWsCnThreads, "the CTA stages both fibers' tables");
 
 struct FiberDesc {
   int64_t slot;      // index of node 0 in the padded state arrays
@@ -138,7 +150,7 @@ int launch_split_step(int K, bool fp64_solve, const StepArgs& a, int n_ctas, voi
 int launch_split_step_expapx(int K, const StepArgs& a, int n_ctas, void* stream);
 int launch_split_step_adaptive(int K, bool fp64_solve, const StepArgs& a, int n_ctas, void* stream);
 // Split roles (split_step_ws.cu): reaction and diffusion warps, two fibers
-// of at most kWsSlot nodes per CTA, tables for K = 12.
+// of at most kWsSlot nodes per CTA, tables for K = kWsKC.
 int launch_split_step_ws(const StepArgs& a, int n_ctas, void* stream);
 size_t split_step_ws_smem_bytes();
 // Surrogate mode's split step (one per launch) with the network-node list

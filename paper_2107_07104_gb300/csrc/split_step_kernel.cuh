@@ -229,7 +229,9 @@ struct SolveCtx {
   bool ie;       // implicit Euler: right-hand side is u itself
 };
 
-template <int K, typename R>
+// CS: stride of the coefficient table and of the PCR buffers (kStride, or
+// the solving threads' count in a kernel that gives the solve fewer threads).
+template <int K, typename R, int CS = kStride>
 __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s, const Exchange<R>& x) {
   R d[K];
   if (s.ie) {
@@ -271,7 +273,7 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
   // back substitution towards the chunk's first row
 #pragma unroll
   for (int j = K - 3; j >= 1; --j) d[j] = d[j] - s.set[j * kCoefPerRow + 2] * d[j + 1];
-  const R D = d[0] - s.cf[kC0 * kStride] * d[1];
+  const R D = d[0] - s.cf[kC0 * CS] * d[1];
   const R E = d[K - 1];
   R y, ym;
   if (s.levels == 0) {
@@ -286,20 +288,20 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
     x.E[s.tid] = E;
     fiber_barrier(s.bar_id, s.Tw);
     const R Dn = (s.p + 1 < s.Tw) ? x.D[s.tid + 1] : (R)0;
-    y = E * s.cf[kKE * kStride] - s.cf[kKD * kStride] * D - s.cf[kKDn * kStride] * Dn;
+    y = E * s.cf[kKE * CS] - s.cf[kKD * CS] * D - s.cf[kKDn * CS] * Dn;
     ym = (R)0;
     if (s.p > 0) {
       const R Dp = x.D[s.tid - 1], Ep = x.E[s.tid - 1];
-      ym = Ep * s.cf[kPKE * kStride] - s.cf[kPKD * kStride] * Dp - s.cf[kPKDn * kStride] * D;
+      ym = Ep * s.cf[kPKE * CS] - s.cf[kPKD * CS] * Dp - s.cf[kPKDn * CS] * D;
     }
   } else {
     x.D[s.tid] = D;
     fiber_barrier(s.bar_id, s.Tw);
     const R Dn = (s.p + 1 < s.Tw) ? x.D[s.tid + 1] : (R)0;
-    R rr = E * s.cf[kKE * kStride] - s.cf[kKD * kStride] * D - s.cf[kKDn * kStride] * Dn;
+    R rr = E * s.cf[kKE * CS] - s.cf[kKD * CS] * D - s.cf[kKDn * CS] * Dn;
     // parallel cyclic reduction over the chunks' last unknowns
     for (int l = 0, st = 1; l < s.levels; ++l, st <<= 1) {
-      R* buf = x.r2 + (l & 1) * kStride;
+      R* buf = x.r2 + (l & 1) * CS;
       buf[s.tid] = rr;
       fiber_barrier(s.bar_id, s.Tw);
       const R rm = (s.p - st >= 0) ? buf[s.tid - st] : (R)0;
@@ -312,7 +314,7 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
     fiber_barrier(s.bar_id, s.Tw);
     ym = (s.p > 0) ? x.y[s.tid - 1] : (R)0;
   }
-  const R xs = D * s.cf[kInvB * kStride] - s.cf[kAb * kStride] * ym - s.cf[kCb * kStride] * y;
+  const R xs = D * s.cf[kInvB * CS] - s.cf[kAb * CS] * ym - s.cf[kCb * CS] * y;
   u[0] = (float)xs;
   u[K - 1] = (float)y;
 #pragma unroll

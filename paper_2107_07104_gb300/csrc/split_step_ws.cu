@@ -9,9 +9,9 @@
 // warp, and the warps of a fiber drift apart over the long reaction phase.
 // Here the two jobs go to different warps of one CTA, which owns two fibers
 // whose state lives in shared memory for a whole launch:
-//   * 12 reaction warps hold 4 nodes per lane and run the Heun substeps of
-//     one fiber while
-//   * 4 diffusion warps (12 nodes per lane) run the two Crank-Nicolson
+//   * kWsReactWarps reaction warps (kWsKR nodes per lane) run the Heun
+//     substeps of one fiber while
+//   * the diffusion warps (kWsKC nodes per lane) run the two Crank-Nicolson
 //     halves between that fiber's reactions on the other fiber,
 // so the fibers alternate: reaction(A) | solve(B), reaction(B) | solve(A).
 // The roles hand fibers over through shared-memory mbarriers: a reaction
@@ -20,21 +20,18 @@
 // warps.  Every wait is bounded; a wait that gives up sets bit 2 of the
 // error flag, and the kernel finishes with its state unreliable instead of
 // hanging.  Results equal the fused kernel's up to rounding order
-// (the same reaction arithmetic; the solve at 12 nodes per thread).
+// (the same reaction arithmetic; the solve at kWsKC nodes per thread).
 #include "split_step_kernel.cuh"
 
 namespace fib {
 namespace {
 
-constexpr int kWsReactWarps = 12;
-constexpr int kWsCnWarps = 4;
-constexpr int kWsThreads = 32 * (kWsReactWarps + kWsCnWarps);
-constexpr int kWsKR = 4;    // nodes per reaction lane
-constexpr int kWsKC = 12;   // nodes per diffusion lane
-constexpr int kWsCnThreads = 32 * kWsCnWarps;
+constexpr int kWsCnWarps = kWsCnThreads / 32;
+constexpr int kWsThreads = 32 * kWsWarps;
 constexpr int kWsSpin = 1 << 20;  // try_wait rounds before a wait gives up
-static_assert(32 * kWsReactWarps * kWsKR == kWsSlot, "reaction warps cover the slot");
-static_assert(kWsCnThreads * kWsKC == kWsSlot, "diffusion warps cover the slot");
+// The diffusion warps' coefficient table and exchange buffers hold one
+// column per diffusion thread.
+constexpr int kWsCS = kWsCnThreads;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -94,22 +91,22 @@ __device__ __forceinline__ Stim stim_init(const StepArgs& a, const FiberDesc& fd
   return s;
 }
 
-__global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kWsThreads, kWsMinBlocks) split_step_ws_kernel(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // layout: state of 2 fibers (u m h n x kWsSlot each), solve tables and
   // exchange buffers of the diffusion warps, 4 mbarriers
   float* st = reinterpret_cast<float*>(smem_raw);                         // [2][4][kWsSlot]
   float* s_rows = st + 2 * 4 * kWsSlot;                                   // [interior | last A | last B] sets
   constexpr int set_len = kWsKC * kCoefPerRow;
-  float* s_coef = s_rows + 3 * set_len;                                   // [2][kNumCoef][kStride]
+  float* s_coef = s_rows + 3 * set_len;                                   // [2][kNumCoef][kWsCS]
   Exchange<float> x;
-  x.first = s_coef + 2 * kNumCoef * kStride;
-  x.last = x.first + kStride;
-  x.D = x.last + kStride;
-  x.E = x.D + kStride;
-  x.y = x.E + kStride;
-  x.r2 = x.y + kStride;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(x.r2 + 2 * kStride);     // ready_R[2], ready_C[2]
+  x.first = s_coef + 2 * kNumCoef * kWsCS;
+  x.last = x.first + kWsCS;
+  x.D = x.last + kWsCS;
+  x.E = x.D + kWsCS;
+  x.y = x.E + kWsCS;
+  x.r2 = x.y + kWsCS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(x.r2 + 2 * kWsCS);       // ready_R[2], ready_C[2]
 
   const int tid = threadIdx.x;
   const int64_t f0 = 2 * (int64_t)blockIdx.x;
@@ -137,11 +134,11 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
   if (tid < 2 * kWsCnThreads) {
     const int q = tid / kWsCnThreads, p = tid % kWsCnThreads;
     const float* rec = g_recs + fd[q].rec + (int64_t)p * a.rec_stride;
-    float* cf = s_coef + q * kNumCoef * kStride;
-    for (int k = 0; k < 7; ++k) cf[k * kStride + p] = rec[k];
-    cf[kPKE * kStride + p] = p > 0 ? rec[4 - a.rec_stride] : 0.0f;
-    cf[kPKD * kStride + p] = p > 0 ? rec[5 - a.rec_stride] : 0.0f;
-    cf[kPKDn * kStride + p] = p > 0 ? rec[6 - a.rec_stride] : 0.0f;
+    float* cf = s_coef + q * kNumCoef * kWsCS;
+    for (int k = 0; k < 7; ++k) cf[k * kWsCS + p] = rec[k];
+    cf[kPKE * kWsCS + p] = p > 0 ? rec[4 - a.rec_stride] : 0.0f;
+    cf[kPKD * kWsCS + p] = p > 0 ? rec[5 - a.rec_stride] : 0.0f;
+    cf[kPKDn * kWsCS + p] = p > 0 ? rec[6 - a.rec_stride] : 0.0f;
   }
   if (tid == 0) {
     mbar_init(&bars[0], kWsCnThreads);  // ready_R[A]: the diffusion warps released fiber A
@@ -156,8 +153,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
   bool abort = false;
   const int warp = tid >> 5;
   if (warp < kWsReactWarps) {
-    // ---- reaction warps: 4 nodes per lane, fibers A, B alternately ----
-    const int q0 = tid;  // nodes [4 q0, 4 q0 + 4)
+    // ---- reaction warps: kWsKR nodes per lane, fibers A, B alternately ----
+    const int q0 = tid;  // nodes [kWsKR q0, kWsKR q0 + kWsKR)
     Stim sm[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) sm[q] = stim_init(a, fd[q], kWsKR * q0, step0);
@@ -168,12 +165,18 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
         mbar_wait(&bars[q], (uint32_t)(s & 1), a.flag, abort);
         if (q < nf) {
           float* base = st + q * 4 * kWsSlot + kWsKR * q0;
-          const float4 vu = *reinterpret_cast<const float4*>(base);
-          const float4 vm = *reinterpret_cast<const float4*>(base + kWsSlot);
-          const float4 vh = *reinterpret_cast<const float4*>(base + 2 * kWsSlot);
-          const float4 vn = *reinterpret_cast<const float4*>(base + 3 * kWsSlot);
-          float u[4] = {vu.x, vu.y, vu.z, vu.w}, m[4] = {vm.x, vm.y, vm.z, vm.w};
-          float h[4] = {vh.x, vh.y, vh.z, vh.w}, n[4] = {vn.x, vn.y, vn.z, vn.w};
+          float u[kWsKR], m[kWsKR], h[kWsKR], n[kWsKR];
+#pragma unroll
+          for (int j = 0; j < kWsKR; j += 4) {
+            const float4 vu = *reinterpret_cast<const float4*>(base + j);
+            const float4 vm = *reinterpret_cast<const float4*>(base + kWsSlot + j);
+            const float4 vh = *reinterpret_cast<const float4*>(base + 2 * kWsSlot + j);
+            const float4 vn = *reinterpret_cast<const float4*>(base + 3 * kWsSlot + j);
+            u[j] = vu.x; u[j + 1] = vu.y; u[j + 2] = vu.z; u[j + 3] = vu.w;
+            m[j] = vm.x; m[j + 1] = vm.y; m[j + 2] = vm.z; m[j + 3] = vm.w;
+            h[j] = vh.x; h[j + 1] = vh.y; h[j + 2] = vh.z; h[j + 3] = vh.w;
+            n[j] = vn.x; n[j + 1] = vn.y; n[j + 2] = vn.z; n[j + 3] = vn.w;
+          }
           Stim& z = sm[q];
           for (int k = 0; k < a.n_sub; ++k) {
             bool on = false;
@@ -188,17 +191,20 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
             if (on) heun_nodes_packed<kWsKR, true, false>(u, m, h, n, a.hh, z.mask);
             else heun_nodes_packed<kWsKR, false, false>(u, m, h, n, a.hh, z.mask);
           }
-          *reinterpret_cast<float4*>(base) = make_float4(u[0], u[1], u[2], u[3]);
-          *reinterpret_cast<float4*>(base + kWsSlot) = make_float4(m[0], m[1], m[2], m[3]);
-          *reinterpret_cast<float4*>(base + 2 * kWsSlot) = make_float4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<float4*>(base + 3 * kWsSlot) = make_float4(n[0], n[1], n[2], n[3]);
+#pragma unroll
+          for (int j = 0; j < kWsKR; j += 4) {
+            *reinterpret_cast<float4*>(base + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+            *reinterpret_cast<float4*>(base + kWsSlot + j) = make_float4(m[j], m[j + 1], m[j + 2], m[j + 3]);
+            *reinterpret_cast<float4*>(base + 2 * kWsSlot + j) = make_float4(h[j], h[j + 1], h[j + 2], h[j + 3]);
+            *reinterpret_cast<float4*>(base + 3 * kWsSlot + j) = make_float4(n[j], n[j + 1], n[j + 2], n[j + 3]);
+          }
         }
         mbar_arrive(&bars[2 + q]);
       }
     }
   } else {
     // ---- diffusion warps: the Crank-Nicolson halves between reactions ----
-    const int p = tid - 32 * kWsReactWarps;  // chunk [12 p, 12 p + 12)
+    const int p = tid - 32 * kWsReactWarps;  // chunk [kWsKC p, kWsKC p + kWsKC)
     SolveCtx<kWsKC, float> sc[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
       sc[q].r = fd[q].n > 1 ? (float)a.r : 0.0f;
       sc[q].ie = false;
       sc[q].rec = g_recs + fd[q].rec + (int64_t)p * a.rec_stride;
-      sc[q].cf = s_coef + q * kNumCoef * kStride + p;
+      sc[q].cf = s_coef + q * kNumCoef * kWsCS + p;
     }
     auto solve = [&](int q, const SolveCtx<kWsKC, float>& scq, int count) {
       float* ub = st + q * 4 * kWsSlot + kWsKC * p;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
         const float4 v = *reinterpret_cast<const float4*>(ub + j);
         u[j] = v.x; u[j + 1] = v.y; u[j + 2] = v.z; u[j + 3] = v.w;
       }
-      for (int c = 0; c < count; ++c) cn_solve<kWsKC, float>(u, scq, x);
+      for (int c = 0; c < count; ++c) cn_solve<kWsKC, float, kWsCS>(u, scq, x);
 #pragma unroll
       for (int j = 0; j < kWsKC; j += 4)
         *reinterpret_cast<float4*>(ub + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) split_step_ws_kernel(const Step
 }  // namespace
 
 size_t split_step_ws_smem_bytes() {
-  return 4 * ((size_t)2 * 4 * kWsSlot + 3 * kWsKC * kCoefPerRow + 2 * kNumCoef * kStride + 7 * kStride) +
+  return 4 * ((size_t)2 * 4 * kWsSlot + 3 * kWsKC * kCoefPerRow + 2 * kNumCoef * kWsCS + 7 * kWsCS) +
          4 * sizeof(uint64_t) + 16;
 }
 

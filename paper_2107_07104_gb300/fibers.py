@@ -22,14 +22,14 @@ from . import build as _build
 _lib = None
 _lock = threading.Lock()
 
-FIB_OK, FIB_EINVAL, FIB_ENOMEM, FIB_ECUDA, FIB_ENONFINITE, FIB_ETIMEOUT, FIB_ESTATE, FIB_ENOTSUP = range(8)
+FIB_OK, FIB_EINVAL, FIB_ENOMEM, FIB_ECUDA, FIB_ENONFINITE, FIB_ETIMEOUT, FIB_ESTATE, FIB_ENOTSUP, FIB_EIO = range(9)
 FIB_MODE_FP32, FIB_MODE_FP64_THOMAS, FIB_MODE_SURROGATE = 0, 1, 2
 FIB_FLAG_ADAPTIVE = 1
 FIB_FLAG_EXP_APPROX = 2
 SPLIT_STRANG_1D0D1D, SPLIT_GODUNOV_1D0D, SPLIT_STRANG_0D1D0D, SPLIT_GODUNOV_0D1D = 0, 1, 2, 3
 DIFFUSION_CRANK_NICOLSON, DIFFUSION_IMPLICIT_EULER = 0, 1
 STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINITE", "FIB_ETIMEOUT",
-                "FIB_ESTATE", "FIB_ENOTSUP"]
+                "FIB_ESTATE", "FIB_ENOTSUP", "FIB_EIO"]
 
 # Every symbol the header declares (checked by the ABI test).
 EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
@@ -39,7 +39,8 @@ EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_s
             "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward", "fibers_adam_step",
             "fibers_feature_stats", "fibers_adaptive_stats", "fibers_solver_tables", "fibers_emg_create",
             "fibers_emg_vm3d", "fibers_emg_phi_e", "fibers_emg_nodes", "fibers_emg_last_error", "fibers_emg_destroy",
-            "fibers_rest_state")
+            "fibers_rest_state", "fibers_autotune_cache_size", "fibers_autotune_cache_clear",
+            "fibers_autotune_cache_save", "fibers_autotune_cache_load")
 SUR_N_PARAMS = 17796
 SUR_BLOB_FLOATS = 3 + 5 + 5 + 4 + 4 + 5 + 5 + 5 + 5 + SUR_N_PARAMS
 SUR_WORK_PER_SAMPLE = 848
@@ -136,8 +137,14 @@ def load(build_if_missing: bool = True):
         L.fibers_emg_last_error.restype = ctypes.c_char_p
         L.fibers_emg_destroy.argtypes = [vp]
         L.fibers_emg_destroy.restype = None
+        L.fibers_autotune_cache_size.argtypes = []
+        L.fibers_autotune_cache_size.restype = i64
+        L.fibers_autotune_cache_clear.argtypes = []
+        L.fibers_autotune_cache_save.argtypes = [ctypes.c_char_p]
+        L.fibers_autotune_cache_load.argtypes = [ctypes.c_char_p]
         for name in ("fibers_load_surrogate", "fibers_hh_reaction", "fibers_mlp_train_step", "fibers_mlp_forward",
-                     "fibers_adam_step", "fibers_feature_stats", "fibers_solver_tables"):
+                     "fibers_adam_step", "fibers_feature_stats", "fibers_solver_tables", "fibers_autotune_cache_clear",
+                     "fibers_autotune_cache_save", "fibers_autotune_cache_load"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
                      "fibers_write_state", "fibers_stats", "fibers_synchronize", "fibers_get_tuning",
@@ -287,6 +294,22 @@ def fibers_autotune(ctx, n_trial_steps: int = 20) -> dict:
     t = FibTuning()
     _check(load().fibers_autotune(ctx, int(n_trial_steps), ctypes.byref(t)), ctx)
     return t.as_dict()
+
+
+def fibers_autotune_cache_size() -> int:
+    return int(load().fibers_autotune_cache_size())
+
+
+def fibers_autotune_cache_clear() -> None:
+    _check(load().fibers_autotune_cache_clear(), None)
+
+
+def fibers_autotune_cache_save(path: str) -> None:
+    _check(load().fibers_autotune_cache_save(os.fsencode(path)), None)
+
+
+def fibers_autotune_cache_load(path: str) -> None:
+    _check(load().fibers_autotune_cache_load(os.fsencode(path)), None)
 
 
 def _dev(t):
