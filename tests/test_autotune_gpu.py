@@ -14,9 +14,9 @@ SHAPE = ("nodes_per_thread", "warps_per_cta", "reaction_pairs", "ctas_per_sm", "
 
 
 def _launches_of_autotune(f, n=5):
-    before = f.kernel_launches()
+    before = f.kernel_launches
     t = f.autotune(n)
-    return f.kernel_launches() - before, t
+    return f.kernel_launches - before, t
 
 
 def test_cache_hit_skips_the_trials_and_keeps_the_simulation(tmp_path):
