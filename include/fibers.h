@@ -190,6 +190,35 @@ fib_status step(fib_ctx* ctx, int64_t n_steps);
  * (section "Code Generation for GPUs"). */
 fib_status read_vm(fib_ctx* ctx, float* out, size_t capacity, int32_t out_is_device);
 
+/* Enqueues the same read of V into host memory without waiting, so that the
+ * copy overlaps the steps enqueued after it (the thesis's copy of the state
+ * subset after a block of GPU steps, section "Code Generation for GPUs",
+ * taken off the critical path).
+ *   out     host memory of >= sum(n_nodes) floats (capacity), ragged order.
+ *           It must stay valid, and the caller must not read it, until
+ *           read_vm_wait on the returned ticket returns.  Page-locked memory
+ *           (cudaHostAlloc, a pinned torch tensor) lets the call return at
+ *           once; with pageable memory it returns after the copy.
+ *   ticket  (nullable) receives this read's number, 0, 1, 2, ... per context.
+ * The values are V after the steps enqueued before the call.  A gather
+ * kernel on the context's stream writes them into one of two device staging
+ * buffers of the context (allocated, with a second stream, on the first
+ * call); the copy to out runs on that second stream.  A third read in flight
+ * makes the GPU, not the host, wait until the first read's copy is done.
+ * Errors: FIB_EINVAL (capacity, out NULL), FIB_ENOMEM, FIB_ECUDA. */
+fib_status read_vm_async(fib_ctx* ctx, float* out, size_t capacity, int64_t* ticket);
+
+/* Waits until the read with this ticket has reached host memory.  Returns
+ * the read's status: FIB_ENONFINITE if a value it read is NaN/Inf (out is
+ * still written), or the step kernels' error (FIB_ETIMEOUT, FIB_ESTATE) as it
+ * stood when the read was taken.  Reads share two staging buffers, so for a
+ * ticket older than the two latest the status is that of the latest read
+ * through the same buffer (errors persist, so none is lost).  Does not wait
+ * for steps enqueued after the read.  fibers_synchronize and fibers_destroy
+ * also wait for every read.  Errors: FIB_EINVAL (ticket never issued),
+ * FIB_ECUDA. */
+fib_status read_vm_wait(fib_ctx* ctx, int64_t ticket);
+
 /* read_vm for callers that cannot allocate device memory.  The thesis has
  * no counterpart to this call; it exists for the library's users.  read_vm
  * with a host buffer stages V through device memory that the context
@@ -255,7 +284,8 @@ fib_status fibers_adaptive_stats(fib_ctx* ctx, int64_t* skipped_fiber_steps);
 /* Waits for all enqueued work and reports device-side errors: FIB_ENONFINITE
  * (state became NaN/Inf), FIB_ESTATE (surrogate node list overflowed),
  * FIB_ETIMEOUT (with split warp roles, a bounded wait between the reaction
- * and diffusion warps gave up; the state is unreliable), FIB_ECUDA.  Thesis: the point of synchronisation between blocks of GPU
+ * and diffusion warps gave up; the state is unreliable), FIB_ECUDA.  Also
+ * waits for every read_vm_async.  Thesis: the point of synchronisation between blocks of GPU
  * timesteps (section "Code Generation for GPUs"). */
 fib_status fibers_synchronize(fib_ctx* ctx);
 

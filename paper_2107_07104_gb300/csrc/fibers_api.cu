@@ -69,6 +69,16 @@ struct fib_ctx {
   float* d_stage = nullptr;  // compact staging (read/write of host buffers)
   size_t stage_elems = 0;
 
+  // read_vm_async: a copy stream, two staging buffers with their status
+  // words, and the events that order them against the steps
+  cudaStream_t copy_stream = nullptr;
+  float* d_async[2] = {nullptr, nullptr};
+  int32_t* d_async_flag = nullptr;  // [2]
+  int32_t* h_async_flag = nullptr;  // [2], page-locked
+  cudaEvent_t ev_gathered[2] = {nullptr, nullptr};
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  int64_t async_issued = 0;
+
   cudaGraphExec_t graph = nullptr;
   int64_t graph_launches = 0;
 
@@ -575,14 +585,18 @@ fib_status build_graph(fib_ctx* c) {
   return FIB_OK;
 }
 
-fib_status check_flag(fib_ctx* c) {
-  int32_t flag = 0;
-  CU(c, cudaMemcpy(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+fib_status flag_status(fib_ctx* c, int32_t flag) {
   if (flag & 4)
     return fail(c, FIB_ETIMEOUT, "a bounded wait between the reaction and diffusion warps gave up; state unreliable");
   if (flag & 2) return fail(c, FIB_ESTATE, "surrogate network-node list overflowed; its entries were dropped");
   if (flag & 1) return fail(c, FIB_ENONFINITE, "state became non-finite (NaN/Inf)");
   return FIB_OK;
+}
+
+fib_status check_flag(fib_ctx* c) {
+  int32_t flag = 0;
+  CU(c, cudaMemcpy(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  return flag_status(c, flag);
 }
 
 // Surrogate mode: the network-node list counters of both step parities
@@ -920,6 +934,59 @@ fib_status read_vm(fib_ctx* c, float* out, size_t capacity, int32_t out_is_devic
   return check_flag(c);
 }
 
+fib_status read_vm_async(fib_ctx* c, float* out, size_t capacity, int64_t* ticket) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (capacity < (size_t)c->total) return fail(c, FIB_EINVAL, "capacity %zu < %lld nodes", capacity, (long long)c->total);
+  if (c->total > 0 && !out) return fail(c, FIB_EINVAL, "out is NULL");
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  if (!c->copy_stream) {
+    CU(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    CU(c, cudaMalloc(&c->d_async_flag, 2 * sizeof(int32_t)));
+    CU(c, cudaHostAlloc(&c->h_async_flag, 2 * sizeof(int32_t), cudaHostAllocDefault));
+    c->h_async_flag[0] = c->h_async_flag[1] = 0;
+    for (int k = 0; k < 2; ++k) {
+      CU(c, cudaEventCreateWithFlags(&c->ev_gathered[k], cudaEventDisableTiming));
+      CU(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+      if (c->total > 0) CU(c, cudaMalloc(&c->d_async[k], sizeof(float) * (size_t)c->total));
+    }
+  }
+  const int k = (int)(c->async_issued & 1);
+  // the staging buffer's previous copy must finish before the gather
+  // overwrites it (a device-side wait: the host does not block)
+  if (c->async_issued >= 2) CU(c, cudaStreamWaitEvent(c->stream, c->ev_copied[k], 0));
+  CU(c, cudaMemsetAsync(c->d_async_flag + k, 0, sizeof(int32_t), c->stream));
+  if (c->total > 0) {
+    fib_status st = check_launch(c, launch_gather_checked(c->d_fibers, c->n_fibers, st_u(c), c->d_async[k],
+                                                          (float)c->p.Vrest, c->d_flag, c->d_async_flag + k, c->stream),
+                                 "gather");
+    if (st != FIB_OK) return st;
+    ++c->launches;
+  } else {
+    CU(c, cudaMemcpyAsync(c->d_async_flag + k, c->d_flag, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CU(c, cudaEventRecord(c->ev_gathered[k], c->stream));
+  CU(c, cudaStreamWaitEvent(c->copy_stream, c->ev_gathered[k], 0));
+  if (c->total > 0)
+    CU(c, cudaMemcpyAsync(out, c->d_async[k], sizeof(float) * (size_t)c->total, cudaMemcpyDeviceToHost,
+                          c->copy_stream));
+  CU(c, cudaMemcpyAsync(c->h_async_flag + k, c->d_async_flag + k, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                        c->copy_stream));
+  CU(c, cudaEventRecord(c->ev_copied[k], c->copy_stream));
+  if (ticket) *ticket = c->async_issued;
+  ++c->async_issued;
+  return FIB_OK;
+}
+
+fib_status read_vm_wait(fib_ctx* c, int64_t ticket) {
+  if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
+  if (ticket < 0 || ticket >= c->async_issued)
+    return fail(c, FIB_EINVAL, "ticket %lld was not issued (%lld issued)", (long long)ticket, (long long)c->async_issued);
+  if (set_device(c) != FIB_OK) return FIB_ECUDA;
+  const int k = (int)(ticket & 1);
+  CU(c, cudaEventSynchronize(c->ev_copied[k]));
+  return flag_status(c, c->h_async_flag[k]);
+}
+
 fib_status fibers_read_state(fib_ctx* c, float* out, size_t capacity, int32_t out_is_device) {
   if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
   const size_t need = 4 * (size_t)c->total;
@@ -995,6 +1062,7 @@ fib_status fibers_synchronize(fib_ctx* c) {
   if (!c) return fail(nullptr, FIB_EINVAL, "ctx is NULL");
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
   CU(c, cudaStreamSynchronize(c->stream));
+  if (c->copy_stream) CU(c, cudaStreamSynchronize(c->copy_stream));
   return check_flag(c);
 }
 
@@ -1484,6 +1552,17 @@ void fibers_destroy(fib_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->d_async[k]);
+    if (c->ev_gathered[k]) cudaEventDestroy(c->ev_gathered[k]);
+    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+  }
+  dfree(c->d_async_flag);
+  if (c->h_async_flag) cudaFreeHost(c->h_async_flag);
   free_layout(c);
   dfree(c->d_mu_off);
   dfree(c->d_fire_k);

@@ -160,6 +160,10 @@ int launch_advance(int64_t* step_base, int64_t n, void* stream);
 // dst[coff + i] = src[slot + i] + add for the n real nodes of every fiber.
 int launch_gather(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,
                   float add, void* stream);
+// launch_gather that also ORs into *out_flag bit 0 for a non-finite value and
+// the step kernels' error bits (*kflag).
+int launch_gather_checked(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst, float add,
+                          const int32_t* kflag, int32_t* out_flag, void* stream);
 // dst[slot + i] = src[coff + i] + add for real nodes; padding nodes keep dst.
 int launch_scatter(const FiberDesc* fibers, int32_t n_fibers, const float* src, float* dst,
                    float add, void* stream);

@@ -32,7 +32,8 @@ STATUS_NAMES = ["FIB_OK", "FIB_EINVAL", "FIB_ENOMEM", "FIB_ECUDA", "FIB_ENONFINI
                 "FIB_ESTATE", "FIB_ENOTSUP", "FIB_EIO"]
 
 # Every symbol the header declares (checked by the ABI test).
-EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
+EXPORTED = ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "read_vm_async",
+            "read_vm_wait", "fibers_read_state",
             "fibers_write_state",
             "fibers_stats", "fibers_synchronize", "fibers_get_tuning", "fibers_set_tuning", "fibers_autotune",
             "fibers_kernel_launches", "fibers_last_error", "fibers_destroy", "fibers_load_surrogate",
@@ -104,6 +105,8 @@ def load(build_if_missing: bool = True):
         L.step.argtypes = [vp, i64]
         L.read_vm.argtypes = [vp, vp, sz, i32]
         L.read_vm_static.argtypes = [vp, vp, sz]
+        L.read_vm_async.argtypes = [vp, vp, sz, P(i64)]
+        L.read_vm_wait.argtypes = [vp, i64]
         L.fibers_read_state.argtypes = [vp, vp, sz, i32]
         L.fibers_write_state.argtypes = [vp, vp, sz, i32, i64]
         L.fibers_stats.argtypes = [vp, P(i64), P(i64)]
@@ -146,7 +149,8 @@ def load(build_if_missing: bool = True):
                      "fibers_adam_step", "fibers_feature_stats", "fibers_solver_tables", "fibers_autotune_cache_clear",
                      "fibers_autotune_cache_save", "fibers_autotune_cache_load"):
             getattr(L, name).restype = ctypes.c_int
-        for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "fibers_read_state",
+        for name in ("fibers_create", "set_stimulus_times", "step", "read_vm", "read_vm_static", "read_vm_async",
+                     "read_vm_wait", "fibers_read_state",
                      "fibers_write_state", "fibers_stats", "fibers_synchronize", "fibers_get_tuning",
                      "fibers_set_tuning", "fibers_autotune"):
             getattr(L, name).restype = ctypes.c_int
@@ -251,6 +255,22 @@ def read_vm_static(ctx, out: np.ndarray) -> None:
     if not isinstance(out, np.ndarray) or out.dtype != np.float32 or not out.flags.c_contiguous:
         raise TypeError("expected a contiguous float32 numpy array")
     _check(load().read_vm_static(ctx, out.ctypes.data, out.size), ctx)
+
+
+def read_vm_async(ctx, out) -> int:
+    """Enqueues a read of V into host memory `out` (a float32 numpy array or a
+    CPU tensor; pinned memory lets the call return at once) and returns its
+    ticket.  `out` must stay alive and unread until read_vm_wait(ticket)."""
+    ptr, n, dev = _buffer(out)
+    if dev:
+        raise TypeError("read_vm_async writes host memory; use read_vm for device buffers")
+    t = ctypes.c_int64(-1)
+    _check(load().read_vm_async(ctx, ptr, n, ctypes.byref(t)), ctx)
+    return int(t.value)
+
+
+def read_vm_wait(ctx, ticket: int) -> None:
+    _check(load().read_vm_wait(ctx, int(ticket)), ctx)
 
 
 def fibers_read_state(ctx, out) -> None:
@@ -484,6 +504,12 @@ class Fibers:
             out = np.empty(self.total, np.float32)
         read_vm(self.ctx, out)
         return out
+
+    def read_vm_async(self, out) -> int:
+        return read_vm_async(self.ctx, out)
+
+    def read_vm_wait(self, ticket: int) -> None:
+        read_vm_wait(self.ctx, ticket)
 
     def read_state(self, out=None):
         if out is None:

@@ -281,6 +281,39 @@ def test_zero_fibers_and_zero_steps():
         assert np.array_equal(before, f.read_state())
 
 
+def _lengths_workload(lengths, seed, n_steps):
+    """Fibers of the given lengths, each motor unit firing once early (at
+    0.05, 0.3, 0.6 and 0.9 ms), so action potentials run in every fiber."""
+    w = W.small_ragged(seed, len(lengths), 5, 5, n_steps)
+    rng = np.random.default_rng(seed)
+    w.n_nodes = np.array(lengths, np.int32)
+    w.junction = W.centre_junctions(rng, w.n_nodes, 0.05)
+    w.mu_of_fiber = (np.arange(len(lengths)) % 4).astype(np.int32)
+    w.mu_offsets = np.arange(5, dtype=np.int64)
+    w.fire_times = np.array([0.05, 0.3, 0.6, 0.9])
+    w.vm0 = (w.params["Vrest"] + rng.normal(0, 0.5, size=w.total_nodes)).astype(np.float32)
+    return w
+
+
+@pytest.mark.parametrize("K,lengths", [
+    (8, [2048, 2047, 1793, 2048]),      # 8 warps x 32 lanes x 8 nodes: the K = 8 maximum
+    (12, [3072, 3071, 2900]),           # the K = 12 maximum
+    (16, [4096, 4095, 4081, 3]),        # the library's longest fiber, beside a 3-node one
+    (0, [4096, 2048, 1481, 1]),         # the automatic shape picks K for the longest
+])
+def test_maximum_lengths_match_the_oracle(K, lengths):
+    """Fibers at the longest length each launch shape holds, and one below,
+    with action potentials running along them."""
+    w = _lengths_workload(lengths, seed=70 + K, n_steps=500)
+    cps = [125, 250, 375, 500]
+    g = gpu_checkpoints(w, cps, tuning=dict(nodes_per_thread=K))
+    o = oracle_checkpoints(w, cps)
+    e = errors(g, o)
+    _report(f"maximum lengths K={K} {lengths}", e)
+    assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
+    assert (o[-1] > 0).sum() >= len(lengths) - 1  # depolarised nodes in the last sample (not the 1-3 node fiber)
+
+
 def test_too_long_fiber_is_rejected():
     w = W.small_ragged(1, 1, 5, 5, 10)
     with pytest.raises(F.FibersError) as ei:
