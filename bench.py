@@ -440,6 +440,8 @@ def run_gpu(args, world, rank, local, dist):
                                "null: the kernel changed since the committed ncu capture"),
             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "kernel": "split_step_kernel", "kernel_ms_per_launch": launch_ms, "launches_timed": len(per_launch),
+            "kernel_ms_per_launch_median": statistics.median(per_launch),
+            "kernel_ms_per_launch_spread": [min(per_launch), max(per_launch)],
             "algorithmic_bytes_per_launch": alg_bytes,
             "algorithmic_bytes": f"{BYTES_PER_NODE_UPDATE:.0f} B per node-update (read + write V, m, h, n in FP32) "
                                  f"x {total} nodes x {S} split steps per launch",
