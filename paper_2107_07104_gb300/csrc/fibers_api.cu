@@ -78,6 +78,7 @@ struct fib_ctx {
   cudaEvent_t ev_gathered[2] = {nullptr, nullptr};
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   int64_t async_issued = 0;
+  bool async_ready = false;
 
   cudaGraphExec_t graph = nullptr;
   int64_t graph_launches = 0;
@@ -646,6 +647,39 @@ fib_status scatter_state(fib_ctx* c, const float* src) {
   return FIB_OK;
 }
 
+// read_vm_async's copy stream, staging buffers, status words and events
+// (all or nothing: free_async undoes a partial setup).
+fib_status setup_async(fib_ctx* c) {
+  CU(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  CU(c, cudaMalloc(&c->d_async_flag, 2 * sizeof(int32_t)));
+  CU(c, cudaHostAlloc(&c->h_async_flag, 2 * sizeof(int32_t), cudaHostAllocDefault));
+  c->h_async_flag[0] = c->h_async_flag[1] = 0;
+  for (int k = 0; k < 2; ++k) {
+    CU(c, cudaEventCreateWithFlags(&c->ev_gathered[k], cudaEventDisableTiming));
+    CU(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+    if (c->total > 0) CU(c, cudaMalloc(&c->d_async[k], sizeof(float) * (size_t)c->total));
+  }
+  return FIB_OK;
+}
+
+void free_async(fib_ctx* c) {
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+    c->copy_stream = nullptr;
+  }
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->d_async[k]);
+    if (c->ev_gathered[k]) cudaEventDestroy(c->ev_gathered[k]);
+    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+    c->ev_gathered[k] = c->ev_copied[k] = nullptr;
+  }
+  dfree(c->d_async_flag);
+  if (c->h_async_flag) cudaFreeHost(c->h_async_flag);
+  c->h_async_flag = nullptr;
+  c->async_ready = false;
+}
+
 }  // namespace
 
 // Surrogate mode, per split step: one launch of the step kernel (the
@@ -939,16 +973,13 @@ fib_status read_vm_async(fib_ctx* c, float* out, size_t capacity, int64_t* ticke
   if (capacity < (size_t)c->total) return fail(c, FIB_EINVAL, "capacity %zu < %lld nodes", capacity, (long long)c->total);
   if (c->total > 0 && !out) return fail(c, FIB_EINVAL, "out is NULL");
   if (set_device(c) != FIB_OK) return FIB_ECUDA;
-  if (!c->copy_stream) {
-    CU(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-    CU(c, cudaMalloc(&c->d_async_flag, 2 * sizeof(int32_t)));
-    CU(c, cudaHostAlloc(&c->h_async_flag, 2 * sizeof(int32_t), cudaHostAllocDefault));
-    c->h_async_flag[0] = c->h_async_flag[1] = 0;
-    for (int k = 0; k < 2; ++k) {
-      CU(c, cudaEventCreateWithFlags(&c->ev_gathered[k], cudaEventDisableTiming));
-      CU(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
-      if (c->total > 0) CU(c, cudaMalloc(&c->d_async[k], sizeof(float) * (size_t)c->total));
+  if (!c->async_ready) {
+    fib_status st = setup_async(c);
+    if (st != FIB_OK) {
+      free_async(c);
+      return st;
     }
+    c->async_ready = true;
   }
   const int k = (int)(c->async_issued & 1);
   // the staging buffer's previous copy must finish before the gather
@@ -1552,17 +1583,7 @@ void fibers_destroy(fib_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->copy_stream) {
-    cudaStreamSynchronize(c->copy_stream);
-    cudaStreamDestroy(c->copy_stream);
-  }
-  for (int k = 0; k < 2; ++k) {
-    dfree(c->d_async[k]);
-    if (c->ev_gathered[k]) cudaEventDestroy(c->ev_gathered[k]);
-    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
-  }
-  dfree(c->d_async_flag);
-  if (c->h_async_flag) cudaFreeHost(c->h_async_flag);
+  free_async(c);
   free_layout(c);
   dfree(c->d_mu_off);
   dfree(c->d_fire_k);
