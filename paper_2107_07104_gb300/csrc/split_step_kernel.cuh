@@ -218,9 +218,35 @@ struct Exchange {  // per-CTA shared buffers, one element per thread
 enum { kInvB = 0, kAb, kCb, kC0, kKE, kKD, kKDn, kPKE, kPKD, kPKDn, kNumCoef };
 constexpr int kStride = 32 * kMaxWarpsPerCta;
 
+// Row coefficients of a chunk in shared memory, coefficient-major: the K
+// values of coefficient c (kF1 .. kBt, the host tables' per-row order) at
+// set[c * K .. c * K + K), so four rows come in one 16-byte load (K is a
+// multiple of 4 and every set starts on a 16-byte boundary).
+enum { kF1 = 0, kF2, kG, kAp, kBt };
+
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// Stages one row set from the host tables' row-major order (row j,
+// coefficient c at j * kCoefPerRow + c) into the coefficient-major order
+// above; threads t0, t0 + stride, ... share the work.
+template <int K, typename R>
+__device__ __forceinline__ void stage_set(R* dst, const R* src, int t0, int stride) {
+  for (int i = t0; i < K * kCoefPerRow; i += stride) {
+    const int j = i / kCoefPerRow, c = i - j * kCoefPerRow;
+    dst[c * K + j] = src[i];
+  }
+}
+
 template <int K, typename R>
 struct SolveCtx {
-  const R* set;  // row coefficients of this thread's chunk (shared memory)
+  const R* set;  // row coefficients of this thread's chunk (shared memory, coefficient-major)
   const R* rec;  // this thread's reduced-system record (global memory)
   const R* cf;   // this thread's column of the coefficient table (shared memory)
   R r;           // c dt_1d / h^2 (0 for single-node fibers)
@@ -266,13 +292,28 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
     }
   }
   }
-  // forward elimination inside the chunk
-  d[1] = d[1] * s.set[1 * kCoefPerRow + 0];
+  // forward elimination inside the chunk (row coefficients four rows at a
+  // time, one vector load per coefficient)
+  {
+    R f1[4], f2[4];
 #pragma unroll
-  for (int j = 2; j < K; ++j) d[j] = d[j] * s.set[j * kCoefPerRow + 0] - s.set[j * kCoefPerRow + 1] * d[j - 1];
+    for (int j = 1; j < K; ++j) {
+      if (j == 1 || (j & 3) == 0) {
+        load4(s.set + kF1 * K + (j & ~3), f1);
+        load4(s.set + kF2 * K + (j & ~3), f2);
+      }
+      d[j] = (j == 1) ? d[1] * f1[1] : d[j] * f1[j & 3] - f2[j & 3] * d[j - 1];
+    }
+  }
   // back substitution towards the chunk's first row
+  {
+    R g[4];
 #pragma unroll
-  for (int j = K - 3; j >= 1; --j) d[j] = d[j] - s.set[j * kCoefPerRow + 2] * d[j + 1];
+    for (int j = K - 3; j >= 1; --j) {
+      if (j == K - 3 || (j & 3) == 3) load4(s.set + kG * K + (j & ~3), g);
+      d[j] = d[j] - g[j & 3] * d[j + 1];
+    }
+  }
   const R D = d[0] - s.cf[kC0 * CS] * d[1];
   const R E = d[K - 1];
   R y, ym;
@@ -317,9 +358,17 @@ __device__ __forceinline__ void cn_solve(float (&u)[K], const SolveCtx<K, R>& s,
   const R xs = D * s.cf[kInvB * CS] - s.cf[kAb * CS] * ym - s.cf[kCb * CS] * y;
   u[0] = (float)xs;
   u[K - 1] = (float)y;
+  {
+    R ap[4], bt[4];
 #pragma unroll
-  for (int j = 1; j < K - 1; ++j)
-    u[j] = (float)(d[j] - s.set[j * kCoefPerRow + 3] * xs - s.set[j * kCoefPerRow + 4] * y);
+    for (int j = 1; j < K - 1; ++j) {
+      if (j == 1 || (j & 3) == 0) {
+        load4(s.set + kAp * K + (j & ~3), ap);
+        load4(s.set + kBt * K + (j & ~3), bt);
+      }
+      u[j] = (float)(d[j] - ap[j & 3] * xs - bt[j & 3] * y);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -432,13 +481,11 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta, MINB)
 
   const WarpMap wm = a.warps[(int64_t)blockIdx.x * a.W + warp];
   const R* g_rows = static_cast<const R*>(a.rows);
-  for (int i = tid; i < set_len; i += B) s_rows[i] = g_rows[i];
+  stage_set<K>(s_rows, g_rows, tid, B);
   FiberDesc fd;
   if (wm.fiber >= 0) {
     fd = a.fibers[wm.fiber];
-    if (warp == wm.first_warp)
-      for (int i = (tid & 31); i < set_len; i += 32)
-        s_rows[(1 + wm.slot) * set_len + i] = g_rows[fd.last_set + i];
+    if (warp == wm.first_warp) stage_set<K>(s_rows + (1 + wm.slot) * set_len, g_rows + fd.last_set, tid & 31, 32);
   }
   __syncthreads();  // every thread of the CTA, before idle warps leave
   if (wm.fiber < 0) return;

@@ -126,10 +126,8 @@ __global__ void __launch_bounds__(kWsThreads, kWsMinBlocks) split_step_ws_kernel
     }
   }
   const float* g_rows = static_cast<const float*>(a.rows);
-  for (int i = tid; i < set_len; i += kWsThreads) {
-    s_rows[i] = g_rows[i];
-    for (int q = 0; q < 2; ++q) s_rows[(1 + q) * set_len + i] = g_rows[fd[q].last_set + i];
-  }
+  stage_set<kWsKC>(s_rows, g_rows, tid, kWsThreads);
+  for (int q = 0; q < 2; ++q) stage_set<kWsKC>(s_rows + (1 + q) * set_len, g_rows + fd[q].last_set, tid, kWsThreads);
   const float* g_recs = static_cast<const float*>(a.recs);
   if (tid < 2 * kWsCnThreads) {
     const int q = tid / kWsCnThreads, p = tid % kWsCnThreads;
