@@ -141,10 +141,13 @@ typedef struct {
   int32_t warp_roles;        /* 1: every warp of a fiber runs both the reaction and the diffusion
                                 solve (the fused kernel); 2: split roles, with 12 reaction warps
                                 (4 nodes per lane) and 4 diffusion warps (12 nodes per lane)
-                                per CTA of two fibers held in shared memory, for fibers of at
-                                most 1536 nodes in FIB_MODE_FP32 with no flags, Strang 1D-0D-1D
-                                and Crank-Nicolson (nodes_per_thread, warps_per_cta,
-                                reaction_pairs and ctas_per_sm then do not apply); 0: automatic */
+                                per CTA of two fibers held in shared memory; 3: split roles in
+                                one 1024-thread CTA per SM of eight fibers, 24 reaction warps (8
+                                nodes per lane) and two groups of 4 diffusion warps.  2 and 3
+                                apply to fibers of at most 1536 nodes in FIB_MODE_FP32 with no
+                                flags, Strang 1D-0D-1D and Crank-Nicolson (nodes_per_thread,
+                                warps_per_cta, reaction_pairs and ctas_per_sm then do not
+                                apply); 0: automatic */
 } fib_tuning;
 
 /* Creates a context for n_fibers fibers and copies the inputs to the device.

@@ -20,6 +20,7 @@
 
 #include "fibers.h"
 #include "fibers_internal.h"
+#include "split_step_ws.h"
 #include "surrogate_internal.h"
 
 #include <cuda_bf16.h>
@@ -46,7 +47,7 @@ struct fib_ctx {
 
   // layout-dependent device data
   int K = 0, W = 0, n_ctas = 0, levels = 0, rec_stride = 0;
-  bool ws = false;  // split warp roles (split_step_ws.cu)
+  int ws = 0;  // split warp roles (split_step_ws.cu): 0 fused kernel, 2 two-fiber shape, 3 eight-fiber shape
   int64_t slots_total = 0;
   float* d_state = nullptr;  // 4 * slots_total
   FiberDesc* d_fibers = nullptr;
@@ -240,6 +241,7 @@ int auto_W(int w_max) { return w_max * std::max(1, kMaxWarpsPerCta / w_max); }
 
 // Whether the automatic shape uses split warp roles where they apply.
 constexpr bool kWsAuto = false;
+constexpr int kWsAutoShape = 2;
 
 void free_layout(fib_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -262,7 +264,7 @@ bool ws_eligible(const fib_ctx* c) {
 
 // Layout of the split-role kernel: slots of kWsSlot nodes, two fibers per
 // CTA, solver tables for kWsKC nodes per diffusion thread.
-fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t) {
+fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t, int shape) {
   constexpr int KC = kWsKC;
   std::map<int32_t, int> cls;
   std::vector<int32_t> lens, tw;
@@ -290,20 +292,22 @@ fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t) {
   }
   const int64_t slot = (int64_t)c->n_fibers * kWsSlot;
   free_layout(c);
-  c->ws = true;
+  const bool wide = shape == 3;
+  const int per_cta = wide ? split_step_ws8_fibers_per_cta() : 2;
+  c->ws = shape;
   c->K = KC;
-  c->W = kWsWarps;
-  c->n_ctas = (c->n_fibers + 1) / 2;
+  c->W = wide ? split_step_ws8_warps() : kWsWarps;
+  c->n_ctas = (c->n_fibers + per_cta - 1) / per_cta;
   c->levels = tab.levels;
   c->rec_stride = tab.rec_stride;
   c->slots_total = slot;
   c->tune.nodes_per_thread = 0;
-  c->tune.warps_per_cta = kWsWarps;
+  c->tune.warps_per_cta = c->W;
   c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
   c->tune.graph_steps = t.graph_steps;
   c->tune.reaction_pairs = 2;
-  c->tune.ctas_per_sm = kWsMinBlocks;
-  c->tune.warp_roles = 2;
+  c->tune.ctas_per_sm = wide ? 1 : kWsMinBlocks;
+  c->tune.warp_roles = shape;
   CU(c, cudaMalloc(&c->d_state, sizeof(float) * 4 * (size_t)slot));
   CU(c, cudaMalloc(&c->d_fibers, sizeof(FiberDesc) * fd.size()));
   CU(c, cudaMalloc(&c->d_warps, sizeof(WarpMap)));
@@ -319,14 +323,14 @@ fib_status build_layout_ws(fib_ctx* c, const fib_tuning& t) {
 // Builds the padded layout, CTA packing and solver tables for tuning t.
 // Allocates (uninitialised) state; the caller fills it.
 fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
-  if (t.warp_roles < 0 || t.warp_roles > 2) return fail(c, FIB_EINVAL, "warp_roles must be 0, 1 or 2");
-  if (t.warp_roles == 2 && !ws_eligible(c))
+  if (t.warp_roles < 0 || t.warp_roles > 3) return fail(c, FIB_EINVAL, "warp_roles must be 0, 1, 2 or 3");
+  if (t.warp_roles >= 2 && !ws_eligible(c))
     return fail(c, FIB_EINVAL,
                 "split warp roles need FIB_MODE_FP32 with no flags, Strang 1D-0D-1D, Crank-Nicolson and fibers of "
                 "at most %d nodes", kWsSlot);
   if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
-  if (t.warp_roles == 2 || (t.warp_roles == 0 && kWsAuto && t.nodes_per_thread == 0 && ws_eligible(c)))
-    return build_layout_ws(c, t);
+  if (t.warp_roles >= 2) return build_layout_ws(c, t, t.warp_roles);
+  if (t.warp_roles == 0 && kWsAuto && t.nodes_per_thread == 0 && ws_eligible(c)) return build_layout_ws(c, t, kWsAutoShape);
   int K = t.nodes_per_thread ? t.nodes_per_thread : auto_K(c->n_nodes);
   if (K != 4 && K != 8 && K != 12 && K != 16) return fail(c, FIB_EINVAL, "nodes_per_thread must be 4, 8, 12 or 16");
   int w_max = 1;
@@ -405,7 +409,7 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   }
 
   free_layout(c);
-  c->ws = false;
+  c->ws = 0;
   c->tune.warp_roles = 1;
   c->K = K;
   c->W = W;
@@ -547,7 +551,8 @@ fib_status enqueue_launches(fib_ctx* c, cudaStream_t s, int64_t offset0, int64_t
   for (int64_t done = 0; done < n; done += S) {
     a.step_offset = offset0 + done;
     a.n_steps = (int32_t)std::min<int64_t>(S, n - done);
-    const int e = c->ws ? launch_split_step_ws(a, c->n_ctas, s)
+    const int e = c->ws == 3 ? launch_split_step_ws8(a, c->n_ctas, s)
+                  : c->ws ? launch_split_step_ws(a, c->n_ctas, s)
                         : launch_split_step(c->K, c->p.mode == FIB_MODE_FP64_THOMAS, a, c->n_ctas, s);
     fib_status st = check_launch(c, e, "split step");
     if (st != FIB_OK) return st;
@@ -1304,6 +1309,8 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
       for (int pairs : {1, 2})
         for (int occ : {2, 3, 4}) cands.push_back(fib_tuning{K, W, start.steps_per_launch, start.graph_steps, pairs, occ, 1});
   }
+  // the two-fiber split-role shape; the eight-fiber one (warp_roles 3) was
+  // slower on every workload measured and is left to explicit requests
   if (ws_eligible(c)) cands.push_back(fib_tuning{0, 0, start.steps_per_launch, start.graph_steps, 0, 0, 2});
   for (const fib_tuning& t : cands) {
     if (build_layout(c, t) != FIB_OK) continue;
@@ -1313,7 +1320,8 @@ fib_status fibers_autotune(fib_ctx* c, int32_t n_trial_steps, fib_tuning* best) 
     a.n_steps = n_trial_steps;
     const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
     auto launch = [&]() {
-      return c->ws ? launch_split_step_ws(a, c->n_ctas, c->stream)
+      return c->ws == 3 ? launch_split_step_ws8(a, c->n_ctas, c->stream)
+             : c->ws ? launch_split_step_ws(a, c->n_ctas, c->stream)
                    : launch_split_step(c->K, fp64, a, c->n_ctas, c->stream);
     };
     // one warm-up launch, then the timed one

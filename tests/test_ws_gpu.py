@@ -1,5 +1,6 @@
-"""The split-role step kernel (dedicated reaction and diffusion warps, two
-fibers per CTA in shared memory) against the FP64 oracle and against the
+"""The split-role step kernels (dedicated reaction and diffusion warps, the
+fibers of a CTA in shared memory: two per CTA with warp_roles 2, eight per
+1024-thread CTA with warp_roles 3) against the FP64 oracle and against the
 fused kernel."""
 import numpy as np
 import pytest
@@ -12,10 +13,11 @@ from parity import (ACT_TIME_MS, MAX_ABS_MV, REL_L2, dense_parity, edge_workload
 
 pytestmark = pytest.mark.gpu
 
-WS = dict(warp_roles=2)
+SHAPES = [2, 3]
 
 
-def test_ragged_lengths_and_a_lone_fiber_match_the_oracle():
+@pytest.mark.parametrize("roles", SHAPES)
+def test_ragged_lengths_and_a_lone_fiber_match_the_oracle(roles):
     # 1..700-node fibers (odd count: the last CTA holds one fiber), junctions
     # at the ends, unstimulated fibers, noisy start; 45-step launches
     w = edge_workload(600)
@@ -25,52 +27,56 @@ def test_ragged_lengths_and_a_lone_fiber_match_the_oracle():
         w.vm0 = w.vm0[:keep]
     assert w.n_fibers % 2 == 1
     cps = list(range(30, w.n_steps + 1, 30))
-    g = gpu_checkpoints(w, cps, tuning=dict(WS, steps_per_launch=45))
+    g = gpu_checkpoints(w, cps, tuning=dict(warp_roles=roles, steps_per_launch=45))
     o = oracle_checkpoints(w, cps)
     e = errors(g, o)
-    print(f"[ws] edge lengths: max|dV| = {e[0]:.3e} mV, rel L2 = {e[1]:.3e}")
+    print(f"[ws{roles}] edge lengths: max|dV| = {e[0]:.3e} mV, rel L2 = {e[1]:.3e}")
     assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
     assert o.max() > 0
 
 
-def test_the_longest_fibers_fill_the_slot():
-    w = W.small_ragged(seed=51, n_fibers=7, lo=1500, hi=1536, n_steps=400)
+@pytest.mark.parametrize("roles", SHAPES)
+def test_the_longest_fibers_fill_the_slot(roles):
+    w = W.small_ragged(seed=51, n_fibers=13, lo=1500, hi=1536, n_steps=400)
     cps = [100, 250, 400]
-    g = gpu_checkpoints(w, cps, tuning=WS)
+    g = gpu_checkpoints(w, cps, tuning=dict(warp_roles=roles))
     o = oracle_checkpoints(w, cps)
     e = errors(g, o)
     assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
 
 
-def test_shape_is_reported_and_graphs_match_eager_launches():
-    w = W.small_ragged(seed=52, n_fibers=12, lo=900, hi=1481, n_steps=300)
+@pytest.mark.parametrize("roles", SHAPES)
+def test_shape_is_reported_and_graphs_match_eager_launches(roles):
+    w = W.small_ragged(seed=52, n_fibers=20, lo=900, hi=1481, n_steps=300)
     out = []
     for graph_steps in (0, 100):
-        with F.Fibers.from_workload(w, tuning=dict(WS, graph_steps=graph_steps)) as f:
-            assert f.tuning["warp_roles"] == 2
+        with F.Fibers.from_workload(w, tuning=dict(warp_roles=roles, graph_steps=graph_steps)) as f:
+            assert f.tuning["warp_roles"] == roles
             f.step(300)
             out.append(f.read_state())
     assert np.array_equal(out[0], out[1])
 
 
-def test_ineligible_contexts_are_rejected():
+@pytest.mark.parametrize("roles", SHAPES)
+def test_ineligible_contexts_are_rejected(roles):
     w = W.small_ragged(seed=53, n_fibers=3, lo=1600, hi=1700, n_steps=10)
     with pytest.raises(F.FibersError) as ei:
-        F.Fibers.from_workload(w, tuning=WS)
+        F.Fibers.from_workload(w, tuning=dict(warp_roles=roles))
     assert ei.value.status == F.FIB_EINVAL
     w2 = W.small_ragged(seed=53, n_fibers=3, lo=100, hi=200, n_steps=10)
     w2.params["flags"] = F.FIB_FLAG_ADAPTIVE
     with pytest.raises(F.FibersError):
-        F.Fibers.from_workload(w2, tuning=WS)
+        F.Fibers.from_workload(w2, tuning=dict(warp_roles=roles))
 
 
-def test_bundle_7744_dense_trajectory_split_roles():
+@pytest.mark.parametrize("roles", SHAPES)
+def test_bundle_7744_dense_trajectory_split_roles(roles):
     """The 7744-fiber bundle, 20 ms, 40 fibers every 10 split steps."""
     w = W.bundle_7744(seed=2, t_end_ms=20.0)
     firing = [f for f in range(w.n_fibers) if w.mu_offsets[w.mu_of_fiber[f] + 1] > w.mu_offsets[w.mu_of_fiber[f]]]
     rng = np.random.default_rng(102)
     fibers = np.unique(np.concatenate([rng.choice(firing, 32, replace=False), W.random_fibers(w.n_fibers, 8, 103)]))
-    r = dense_parity(w, fibers, 10, tuning=dict(WS, graph_steps=100))
-    print(f"[ws] bundle 7744: max|dV| = {r['max_abs']:.3e} mV, rel L2 = {r['rel_l2']:.3e}, act {r['act']:.3e} ms")
+    r = dense_parity(w, fibers, 10, tuning=dict(warp_roles=roles, graph_steps=100))
+    print(f"[ws{roles}] bundle 7744: max|dV| = {r['max_abs']:.3e} mV, rel L2 = {r['rel_l2']:.3e}, act {r['act']:.3e} ms")
     assert r["max_abs"] <= MAX_ABS_MV and r["rel_l2"] <= REL_L2 and r["act"] <= ACT_TIME_MS
     assert r["same_activated"]
