@@ -219,7 +219,8 @@ fib_status read_vm_async(fib_ctx* ctx, float* out, size_t capacity, int64_t* tic
  * through the same buffer (errors persist, so none is lost).  Does not wait
  * for steps enqueued after the read.  fibers_synchronize and fibers_destroy
  * also wait for every read.  Errors: FIB_EINVAL (ticket never issued),
- * FIB_ECUDA. */
+ * FIB_ECUDA.  Thesis: the end of the state copy of read_vm_async (section
+ * "Code Generation for GPUs"). */
 fib_status read_vm_wait(fib_ctx* ctx, int64_t ticket);
 
 /* read_vm for callers that cannot allocate device memory.  The thesis has
@@ -358,7 +359,9 @@ fib_status fibers_autotune_cache_load(const char* path);
  *             rest an exact fixed point), theta[17796].
  * raw = (u, m, h, n, s). 
  * Copied; the caller keeps the blob.  Errors: FIB_EINVAL (size, shape,
- * non-finite values, in_sigma <= 0), FIB_ESTATE (not a surrogate context). */
+ * non-finite values, in_sigma <= 0), FIB_ESTATE (not a surrogate context).
+ * No thesis counterpart: the surrogate is this library's addition (see the
+ * section comment above). */
 fib_status fibers_load_surrogate(fib_ctx* ctx, const float* blob, size_t n_floats);
 
 /* The plain reaction step (dt_split / dt_0d Heun substeps of the HH model,
@@ -382,12 +385,14 @@ fib_status fibers_hh_reaction(const fib_params* p, int64_t count, const float* i
  *   theta     17796 floats.      x       batch x 5 normalised inputs.
  *   target    batch x 4.         workspace >= batch x 848 floats (scratch).
  *   grad      17796 floats (out). loss   1 float (out, device).
- * Asynchronous.  Errors: FIB_EINVAL, FIB_ECUDA. */
+ * Asynchronous.  Errors: FIB_EINVAL, FIB_ECUDA.  No thesis counterpart
+ * (training of the surrogate network). */
 fib_status fibers_mlp_train_step(const float* theta, int32_t quantize, const float* x, const float* target,
                                  int64_t batch, float* workspace, float* grad, float* loss, void* cuda_stream);
 
 /* Forward pass only: out (batch x 4) for inputs x (batch x 5); workspace >=
- * batch x 520 floats.  Asynchronous. */
+ * batch x 520 floats.  Asynchronous.  Errors: FIB_EINVAL, FIB_ECUDA.  No
+ * thesis counterpart (the surrogate network). */
 fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float* x, int64_t batch, float* workspace,
                               float* out, void* cuda_stream);
 
@@ -400,13 +405,15 @@ fib_status fibers_mlp_forward(const float* theta, int32_t quantize, const float*
  *              example with theta before the first step).
  *   avg_decay  in [0, 1]; ignored when theta_avg is NULL.
  * Asynchronous.  Errors: FIB_EINVAL (n < 1, t < 1, a NULL buffer, avg_decay
- * outside [0, 1]), FIB_ECUDA. */
+ * outside [0, 1]), FIB_ECUDA.  No thesis counterpart (surrogate training). */
 fib_status fibers_adam_step(float* theta, float* m, float* v, const float* grad, int64_t n, float lr, float beta1,
                             float beta2, float eps, int64_t t, float* theta_avg, float avg_decay, void* cuda_stream);
 
 /* Per-column mean, standard deviation, minimum and maximum of a device matrix
  * X (n x cols, row-major) into out (host, 4 x cols doubles, column by column:
- * mean, std, min, max).  Synchronises cuda_stream.  cols <= 64. */
+ * mean, std, min, max).  Synchronises cuda_stream.  cols <= 64.  Errors:
+ * FIB_EINVAL, FIB_ECUDA.  No thesis counterpart (input normalisation of the
+ * surrogate network). */
 fib_status fibers_feature_stats(const float* X, int64_t n, int32_t cols, double* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
@@ -448,14 +455,16 @@ typedef struct {
  * object, which owns its device memory (mapping in CSR form, about 8 x 8
  * bytes per fiber node).  Synchronises.  Errors: FIB_EINVAL (sizes,
  * spacing, conductivities, non-finite positions; message on ctx),
- * FIB_ENOMEM, FIB_ECUDA, FIB_ENOTSUP (no cooperative launch). */
+ * FIB_ENOMEM, FIB_ECUDA, FIB_ENOTSUP (no cooperative launch).  Thesis:
+ * sec:data_mapping_between_meshes, eq:mapping_source_target. */
 fib_status fibers_emg_create(fib_ctx* ctx, const double* fiber_xy, double z0, const fib_mesh3d* mesh,
                              fib_emg** out);
 
 /* V3D (mV, FP64) of every 3D node for the fibers' current V, into out
  * (capacity >= nx ny nz; out_is_device selects device or host memory).
  * Synchronises.  Errors: FIB_EINVAL, FIB_ECUDA (message:
- * fibers_emg_last_error). */
+ * fibers_emg_last_error).  Thesis: eq:discretized_fibers_2 (the prolongation
+ * of V onto the 3D mesh). */
 fib_status fibers_emg_vm3d(fib_emg* emg, double* out, size_t capacity, int32_t out_is_device);
 
 /* phi_e (mV, written as float) of every 3D node for the fibers' current V:
@@ -464,17 +473,19 @@ fib_status fibers_emg_vm3d(fib_emg* emg, double* out, size_t capacity, int32_t o
  * the right-hand side's norm, or after max_iter iterations.  iterations and
  * rel_residual (nullable) receive what the solve reached.  Synchronises.
  * Errors: FIB_EINVAL, FIB_ECUDA, FIB_ETIMEOUT (rtol not reached; out holds
- * the last iterate). */
+ * the last iterate).  Thesis: eq:discretized_fibers_3, eq:static_bidomain_rhs. */
 fib_status fibers_emg_phi_e(fib_emg* emg, float* out, size_t capacity, int32_t out_is_device, double rtol,
                             int32_t max_iter, int32_t* iterations, double* rel_residual);
 
-/* Number of 3D nodes (0 for NULL). */
+/* Number of 3D nodes (0 for NULL).  No thesis counterpart. */
 int64_t fibers_emg_nodes(const fib_emg* emg);
 
-/* Message of the last failing call on emg (never NULL). */
+/* Message of the last failing call on emg (never NULL).  No thesis
+ * counterpart. */
 const char* fibers_emg_last_error(const fib_emg* emg);
 
-/* Frees the mapping and solver memory.  NULL is allowed. */
+/* Frees the mapping and solver memory.  NULL is allowed.  No thesis
+ * counterpart. */
 void fibers_emg_destroy(fib_emg* emg);
 
 /* Host-only diagnostic (no GPU needed): the coefficient tables of the
