@@ -411,6 +411,7 @@ def run_gpu(args, world, rank, local, dist):
     legs = {}
     if not args.no_legs:
         legs["bundle_7744"] = bundle_7744_leg(args, stream, dev)
+        legs["split_roles"] = split_roles_leg(args, stream, dev)
         legs["ragged_20000"] = ragged_leg(args, stream, dev)
         if not args.no_surrogate:
             legs["surrogate"] = surrogate_leg(args, stream, dev)
@@ -511,6 +512,26 @@ def bundle_7744_leg(args, stream, dev, steps=1000):
     return {"workload": "bundle 7744 fibers x 1481 nodes (88x88), 100 MUs, Poisson 10-30 Hz",
             "node_updates_per_s": rate, "ms_per_split_step": ms / steps, "split_steps": steps, "finite": finite,
             "hbm_frac_at_32_bytes": rate * BYTES_PER_NODE_UPDATE / 1e9 / hbm_peak}
+
+
+def split_roles_leg(args, stream, dev, steps=1000):
+    """The launch shapes of the step kernel on the headline workload: the
+    fused kernel and the two split-role shapes (reaction and diffusion on
+    separate warps), each timed over the same steps in 100-step graphs."""
+    from paper_2107_07104_gb300 import fibers as F
+    w = rank_workload(0, args.workload)
+    out = {"workload": WORKLOADS[args.workload][0], "split_steps": steps}
+    for roles, name in ((1, "fused"), (2, "split roles, 2 fibers per CTA"), (3, "split roles, 8 fibers per CTA")):
+        with F.Fibers.from_workload(w, tuning=dict(graph_steps=100, warp_roles=roles), stream=stream) as fib:
+            fib.step(200)
+            ms = time_steps(fib, stream, dev, steps, 100)
+            finite = bool(np.isfinite(fib.read_vm()).all())
+        out[name] = {"warp_roles": roles, "node_updates_per_s": float(w.total_nodes) * steps / (ms / 1e3),
+                     "ms_per_split_step": ms / steps, "finite": finite}
+    base = out["fused"]["node_updates_per_s"]
+    for k in ("split roles, 2 fibers per CTA", "split roles, 8 fibers per CTA"):
+        out[k]["vs_fused"] = out[k]["node_updates_per_s"] / base
+    return out
 
 
 def ragged_leg(args, stream, dev, steps=2000):
