@@ -92,6 +92,61 @@ __device__ __forceinline__ Stim stim_init(const StepArgs& a, const FiberDesc& fd
   return s;
 }
 
+// One split step's reaction (n_sub Heun substeps, eq:heun, with the motor
+// unit's stimulus) on the KR nodes of one lane, read from and written back
+// to a fiber's state in shared memory (u, m, h, n rows kWsSlot apart).
+template <int KR>
+__device__ __forceinline__ void react_lane(const StepArgs& a, float* base, Stim& z, int64_t stp) {
+  float u[KR], m[KR], h[KR], n[KR];
+#pragma unroll
+  for (int j = 0; j < KR; j += 4) {
+    const float4 vu = *reinterpret_cast<const float4*>(base + j);
+    const float4 vm = *reinterpret_cast<const float4*>(base + kWsSlot + j);
+    const float4 vh = *reinterpret_cast<const float4*>(base + 2 * kWsSlot + j);
+    const float4 vn = *reinterpret_cast<const float4*>(base + 3 * kWsSlot + j);
+    u[j] = vu.x; u[j + 1] = vu.y; u[j + 2] = vu.z; u[j + 3] = vu.w;
+    m[j] = vm.x; m[j + 1] = vm.y; m[j + 2] = vm.z; m[j + 3] = vm.w;
+    h[j] = vh.x; h[j + 1] = vh.y; h[j + 2] = vh.z; h[j + 3] = vh.w;
+    n[j] = vn.x; n[j + 1] = vn.y; n[j + 2] = vn.z; n[j + 3] = vn.w;
+  }
+  for (int k = 0; k < a.n_sub; ++k) {
+    bool on = false;
+    if (z.mask) {
+      const int64_t kk = stp * a.n_sub + k;
+      while (z.fk != INT64_MAX && z.fk + a.pulse <= kk) {
+        ++z.cur;
+        z.fk = z.cur < z.fend ? a.fire_k[z.cur] : INT64_MAX;
+      }
+      on = z.fk <= kk;
+    }
+    if (on) heun_nodes_packed<KR, true, false>(u, m, h, n, a.hh, z.mask);
+    else heun_nodes_packed<KR, false, false>(u, m, h, n, a.hh, z.mask);
+  }
+#pragma unroll
+  for (int j = 0; j < KR; j += 4) {
+    *reinterpret_cast<float4*>(base + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+    *reinterpret_cast<float4*>(base + kWsSlot + j) = make_float4(m[j], m[j + 1], m[j + 2], m[j + 3]);
+    *reinterpret_cast<float4*>(base + 2 * kWsSlot + j) = make_float4(h[j], h[j + 1], h[j + 2], h[j + 3]);
+    *reinterpret_cast<float4*>(base + 3 * kWsSlot + j) = make_float4(n[j], n[j + 1], n[j + 2], n[j + 3]);
+  }
+}
+
+// count Crank-Nicolson solves of one fiber's u row (kWsKC nodes per
+// thread, chunk p), in and out of shared memory.
+__device__ __forceinline__ void solve_chunk(float* ub, const SolveCtx<kWsKC, float>& sc, const Exchange<float>& x,
+                                            int count) {
+  float u[kWsKC];
+#pragma unroll
+  for (int j = 0; j < kWsKC; j += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(ub + j);
+    u[j] = v.x; u[j + 1] = v.y; u[j + 2] = v.z; u[j + 3] = v.w;
+  }
+  for (int c = 0; c < count; ++c) cn_solve<kWsKC, float, kWsCS>(u, sc, x);
+#pragma unroll
+  for (int j = 0; j < kWsKC; j += 4)
+    *reinterpret_cast<float4*>(ub + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+}
+
 __global__ void __launch_bounds__(kWsThreads, kWsMinBlocks) split_step_ws_kernel(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // layout: state of 2 fibers (u m h n x kWsSlot each), solve tables and
@@ -164,39 +219,7 @@ __global__ void __launch_bounds__(kWsThreads, kWsMinBlocks) split_step_ws_kernel
         mbar_wait(&bars[q], (uint32_t)(s & 1), a.flag, abort);
         if (q < nf) {
           float* base = st + q * 4 * kWsSlot + kWsKR * q0;
-          float u[kWsKR], m[kWsKR], h[kWsKR], n[kWsKR];
-#pragma unroll
-          for (int j = 0; j < kWsKR; j += 4) {
-            const float4 vu = *reinterpret_cast<const float4*>(base + j);
-            const float4 vm = *reinterpret_cast<const float4*>(base + kWsSlot + j);
-            const float4 vh = *reinterpret_cast<const float4*>(base + 2 * kWsSlot + j);
-            const float4 vn = *reinterpret_cast<const float4*>(base + 3 * kWsSlot + j);
-            u[j] = vu.x; u[j + 1] = vu.y; u[j + 2] = vu.z; u[j + 3] = vu.w;
-            m[j] = vm.x; m[j + 1] = vm.y; m[j + 2] = vm.z; m[j + 3] = vm.w;
-            h[j] = vh.x; h[j + 1] = vh.y; h[j + 2] = vh.z; h[j + 3] = vh.w;
-            n[j] = vn.x; n[j + 1] = vn.y; n[j + 2] = vn.z; n[j + 3] = vn.w;
-          }
-          Stim& z = sm[q];
-          for (int k = 0; k < a.n_sub; ++k) {
-            bool on = false;
-            if (z.mask) {
-              const int64_t kk = stp * a.n_sub + k;
-              while (z.fk != INT64_MAX && z.fk + a.pulse <= kk) {
-                ++z.cur;
-                z.fk = z.cur < z.fend ? a.fire_k[z.cur] : INT64_MAX;
-              }
-              on = z.fk <= kk;
-            }
-            if (on) heun_nodes_packed<kWsKR, true, false>(u, m, h, n, a.hh, z.mask);
-            else heun_nodes_packed<kWsKR, false, false>(u, m, h, n, a.hh, z.mask);
-          }
-#pragma unroll
-          for (int j = 0; j < kWsKR; j += 4) {
-            *reinterpret_cast<float4*>(base + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
-            *reinterpret_cast<float4*>(base + kWsSlot + j) = make_float4(m[j], m[j + 1], m[j + 2], m[j + 3]);
-            *reinterpret_cast<float4*>(base + 2 * kWsSlot + j) = make_float4(h[j], h[j + 1], h[j + 2], h[j + 3]);
-            *reinterpret_cast<float4*>(base + 3 * kWsSlot + j) = make_float4(n[j], n[j + 1], n[j + 2], n[j + 3]);
-          }
+          react_lane<kWsKR>(a, base, sm[q], stp);
         }
         mbar_arrive(&bars[2 + q]);
       }
@@ -222,19 +245,6 @@ __global__ void __launch_bounds__(kWsThreads, kWsMinBlocks) split_step_ws_kernel
       sc[q].rec = g_recs + fd[q].rec + (int64_t)p * a.rec_stride;
       sc[q].cf = s_coef + q * kNumCoef * kWsCS + p;
     }
-    auto solve = [&](int q, const SolveCtx<kWsKC, float>& scq, int count) {
-      float* ub = st + q * 4 * kWsSlot + kWsKC * p;
-      float u[kWsKC];
-#pragma unroll
-      for (int j = 0; j < kWsKC; j += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(ub + j);
-        u[j] = v.x; u[j + 1] = v.y; u[j + 2] = v.z; u[j + 3] = v.w;
-      }
-      for (int c = 0; c < count; ++c) cn_solve<kWsKC, float, kWsCS>(u, scq, x);
-#pragma unroll
-      for (int j = 0; j < kWsKC; j += 4)
-        *reinterpret_cast<float4*>(ub + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
-    };
     for (int s = 0; s <= S; ++s) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(kWsThreads, kWsMinBlocks) split_step_ws_kernel
         // and the first half of step s
         if (s > 0) mbar_wait(&bars[2 + q], (uint32_t)((s - 1) & 1), a.flag, abort);
         const int count = (s > 0 ? a.n_cn : 0) + (s < S ? a.n_cn : 0);
-        if (q < nf) solve(q, sc[q], count);  // all diffusion warps take the same branch
+        if (q < nf) solve_chunk(st + q * 4 * kWsSlot + kWsKC * p, sc[q], x, count);  // uniform over the warps
         if (s < S) mbar_arrive(&bars[q]);
       }
     }
@@ -376,39 +386,7 @@ __global__ void __launch_bounds__(kW8Threads, 1) split_step_ws8_kernel(const Ste
         const int fc = q * kW8Set + fi;
         if (fc < nf) {
           float* base = st + fc * 4 * kWsSlot + node0;
-          float u[kW8KR], m[kW8KR], h[kW8KR], n[kW8KR];
-#pragma unroll
-          for (int j = 0; j < kW8KR; j += 4) {
-            const float4 vu = *reinterpret_cast<const float4*>(base + j);
-            const float4 vm = *reinterpret_cast<const float4*>(base + kWsSlot + j);
-            const float4 vh = *reinterpret_cast<const float4*>(base + 2 * kWsSlot + j);
-            const float4 vn = *reinterpret_cast<const float4*>(base + 3 * kWsSlot + j);
-            u[j] = vu.x; u[j + 1] = vu.y; u[j + 2] = vu.z; u[j + 3] = vu.w;
-            m[j] = vm.x; m[j + 1] = vm.y; m[j + 2] = vm.z; m[j + 3] = vm.w;
-            h[j] = vh.x; h[j + 1] = vh.y; h[j + 2] = vh.z; h[j + 3] = vh.w;
-            n[j] = vn.x; n[j + 1] = vn.y; n[j + 2] = vn.z; n[j + 3] = vn.w;
-          }
-          Stim& z = sm[q];
-          for (int k = 0; k < a.n_sub; ++k) {
-            bool on = false;
-            if (z.mask) {
-              const int64_t kk = stp * a.n_sub + k;
-              while (z.fk != INT64_MAX && z.fk + a.pulse <= kk) {
-                ++z.cur;
-                z.fk = z.cur < z.fend ? a.fire_k[z.cur] : INT64_MAX;
-              }
-              on = z.fk <= kk;
-            }
-            if (on) heun_nodes_packed<kW8KR, true, false>(u, m, h, n, a.hh, z.mask);
-            else heun_nodes_packed<kW8KR, false, false>(u, m, h, n, a.hh, z.mask);
-          }
-#pragma unroll
-          for (int j = 0; j < kW8KR; j += 4) {
-            *reinterpret_cast<float4*>(base + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
-            *reinterpret_cast<float4*>(base + kWsSlot + j) = make_float4(m[j], m[j + 1], m[j + 2], m[j + 3]);
-            *reinterpret_cast<float4*>(base + 2 * kWsSlot + j) = make_float4(h[j], h[j + 1], h[j + 2], h[j + 3]);
-            *reinterpret_cast<float4*>(base + 3 * kWsSlot + j) = make_float4(n[j], n[j + 1], n[j + 2], n[j + 3]);
-          }
+          react_lane<kW8KR>(a, base, sm[q], stp);
         }
         mbar_arrive(&bars[2 + q]);
       }
@@ -461,17 +439,7 @@ __global__ void __launch_bounds__(kW8Threads, 1) split_step_ws8_kernel(const Ste
           sc.ie = false;
           sc.rec = rec;
           sc.cf = cfb + p;
-          float* ub = st + fc * 4 * kWsSlot + kWsKC * p;
-          float u[kWsKC];
-#pragma unroll
-          for (int j = 0; j < kWsKC; j += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(ub + j);
-            u[j] = v.x; u[j + 1] = v.y; u[j + 2] = v.z; u[j + 3] = v.w;
-          }
-          for (int e = 0; e < count; ++e) cn_solve<kWsKC, float, kWsCS>(u, sc, x);
-#pragma unroll
-          for (int j = 0; j < kWsKC; j += 4)
-            *reinterpret_cast<float4*>(ub + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+          solve_chunk(st + fc * 4 * kWsSlot + kWsKC * p, sc, x, count);
         }
         if (s < S) mbar_arrive(&bars[q]);
       }
