@@ -80,3 +80,34 @@ def test_bundle_7744_dense_trajectory_split_roles(roles):
     print(f"[ws{roles}] bundle 7744: max|dV| = {r['max_abs']:.3e} mV, rel L2 = {r['rel_l2']:.3e}, act {r['act']:.3e} ms")
     assert r["max_abs"] <= MAX_ABS_MV and r["rel_l2"] <= REL_L2 and r["act"] <= ACT_TIME_MS
     assert r["same_activated"]
+
+
+@pytest.mark.parametrize("roles", SHAPES)
+def test_checkpoint_resume_and_switching_shapes(roles):
+    """A split-role run resumed from its checkpoint gives the same bits; a
+    re-layout between the fused kernel and a split-role shape keeps the state
+    bit for bit, and the mixed run stays on the oracle's trajectory."""
+    w = W.small_ragged(seed=54, n_fibers=19, lo=700, hi=1536, n_steps=400)
+    t = dict(warp_roles=roles)
+    with F.Fibers.from_workload(w, tuning=t) as f:
+        f.step(400)
+        full = f.read_state()
+    with F.Fibers.from_workload(w, tuning=t) as f:
+        f.step(150)
+        st = f.read_state()
+        idx, _ = f.stats()
+    with F.Fibers.from_workload(w, tuning=t) as f:
+        f.write_state(st, idx)
+        f.step(250)
+        assert np.array_equal(f.read_state(), full)
+    with F.Fibers.from_workload(w, tuning=dict(warp_roles=1)) as f:
+        f.step(200)
+        before = f.read_state()
+        f.set_tuning(t)
+        assert f.tuning["warp_roles"] == roles
+        assert np.array_equal(f.read_state(), before)
+        f.step(200)
+        mixed = f.read_vm().astype(np.float64)
+    o = oracle_checkpoints(w, [400])[0]
+    e = errors(mixed[None, :], o[None, :])
+    assert e[0] <= MAX_ABS_MV and e[1] <= REL_L2
