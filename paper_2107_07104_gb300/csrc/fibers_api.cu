@@ -213,13 +213,19 @@ int warps_for(int32_t n, int K) {
   return (int)std::min<int64_t>((T + 31) / 32, INT32_MAX);
 }
 
-int auto_K(const std::vector<int32_t>& n_nodes) {
-  // K = 8 (measured fastest on GB300 with packed pairs and the 80-register
-  // budget) whenever every fiber fits; otherwise the fewest padded nodes
+// Nodes per thread when the caller leaves it open.  The plain FP32 step
+// (exact or exp* exponentials) runs fastest at K = 12 on GB300 (packed pairs,
+// 8-warp CTAs, the 80-register budget: 0.893 ms per split step on the
+// 67,600-fiber bundle against 0.927 at K = 8); the surrogate step (one split
+// step per launch) and adaptive computation measured faster at K = 8, as
+// does the FP64 solve's register budget.  Longer fibers take the K that
+// fits them with the fewest padded nodes.
+int auto_K(const std::vector<int32_t>& n_nodes, bool plain_fp32) {
   int max_n = 0;
   for (int32_t n : n_nodes) max_n = std::max(max_n, n);
-  if (warps_for(max_n, 8) <= kMaxWarpsPerCta) return 8;
-  int best = 12;
+  const int first = plain_fp32 ? 12 : 8;
+  if (warps_for(max_n, first) <= kMaxWarpsPerCta) return first;
+  int best = 16;
   int64_t best_pad = -1;
   for (int K : {12, 16}) {
     int64_t pad = 0;
@@ -331,7 +337,8 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   if (t.steps_per_launch < 0 || t.graph_steps < 0) return fail(c, FIB_EINVAL, "negative steps in tuning");
   if (t.warp_roles >= 2) return build_layout_ws(c, t, t.warp_roles);
   if (t.warp_roles == 0 && kWsAuto && t.nodes_per_thread == 0 && ws_eligible(c)) return build_layout_ws(c, t, kWsAutoShape);
-  int K = t.nodes_per_thread ? t.nodes_per_thread : auto_K(c->n_nodes);
+  const bool plain_fp32 = c->p.mode == FIB_MODE_FP32 && !(c->p.flags & FIB_FLAG_ADAPTIVE);
+  int K = t.nodes_per_thread ? t.nodes_per_thread : auto_K(c->n_nodes, plain_fp32);
   if (K != 4 && K != 8 && K != 12 && K != 16) return fail(c, FIB_EINVAL, "nodes_per_thread must be 4, 8, 12 or 16");
   int w_max = 1;
   for (int32_t n : c->n_nodes) w_max = std::max(w_max, warps_for(n, K));
@@ -422,7 +429,7 @@ fib_status build_layout(fib_ctx* c, const fib_tuning& t) {
   c->tune.steps_per_launch = t.steps_per_launch ? t.steps_per_launch : 100;
   c->tune.graph_steps = t.graph_steps;
   c->tune.reaction_pairs = t.reaction_pairs ? t.reaction_pairs : 2;
-  c->tune.ctas_per_sm = t.ctas_per_sm ? t.ctas_per_sm : (K == 8 ? 3 : 2);
+  c->tune.ctas_per_sm = t.ctas_per_sm ? t.ctas_per_sm : 3;
 
   const bool fp64 = c->p.mode == FIB_MODE_FP64_THOMAS;
   const size_t es = fp64 ? 8 : 4;

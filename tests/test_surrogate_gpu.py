@@ -114,10 +114,15 @@ def _exclude_all_blob():
                        np.ones(4, np.float32), lo, hi, lo, hi)
 
 
-def test_fallback_reproduces_the_plain_path_bit_for_bit():
+@pytest.mark.parametrize("K", [8, 12])
+def test_fallback_reproduces_the_plain_path_bit_for_bit(K):
+    """With every node outside the envelope the surrogate step is the plain
+    step, bit for bit, in the same launch shape (the automatic shapes of the
+    two modes differ: K = 8 for the surrogate step, 12 for the plain one)."""
     w = W.small_ragged(seed=31, n_fibers=24, lo=1, hi=700, n_steps=300)
-    plain = gpu_checkpoints(w, [150, 300])
-    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE) as f:
+    t = dict(nodes_per_thread=K)
+    plain = gpu_checkpoints(w, [150, 300], tuning=t)
+    with F.Fibers.from_workload(w, mode=F.FIB_MODE_SURROGATE, tuning=t) as f:
         with pytest.raises(F.FibersError) as ei:
             f.step(1)  # no surrogate loaded yet
         assert ei.value.status == F.FIB_ESTATE
